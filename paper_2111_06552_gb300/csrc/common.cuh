@@ -1,0 +1,82 @@
+// Shared device/host helpers of the GCG library (internal header, not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/gcge.h"
+
+namespace gcge {
+
+// --------------------------------------------------------------------------- errors
+struct CudaError {
+  cudaError_t err;
+  const char *file;
+  int line;
+};
+
+// Records the first CUDA error seen by a handle-less call so that
+// gcge_last_error_message() can report it.
+void record_cuda_error(cudaError_t e, const char *file, int line);
+
+#define GCGE_CUDA(...)                                                       \
+  do {                                                                       \
+    cudaError_t _e = (__VA_ARGS__);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      ::gcge::record_cuda_error(_e, __FILE__, __LINE__);                     \
+      return GCGE_ECUDA;                                                     \
+    }                                                                        \
+  } while (0)
+
+#define GCGE_CHECK(...)                                                      \
+  do {                                                                       \
+    int _s = (__VA_ARGS__);                                                         \
+    if (_s != GCGE_OK) return _s;                                            \
+  } while (0)
+
+#define GCGE_LAUNCH_CHECK() GCGE_CUDA(cudaGetLastError())
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int64_t round_up(int64_t a, int64_t b) { return ((a + b - 1) / b) * b; }
+
+constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs; grids are sized in multiples of this
+
+int device_sm_count();         // queried once, falls back to kNumSMs
+
+// --------------------------------------------------------------------------- device helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = v > w ? v : w;
+  }
+  return v;
+}
+
+// Block-wide sum; `sh` must hold blockDim.x/32 elements. Result valid in all threads.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace gcge

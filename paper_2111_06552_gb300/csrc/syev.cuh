@@ -1,0 +1,24 @@
+// Dense FP64 symmetric eigensolver on the device (STEP 3's dsyevx role) -- internal.
+#pragma once
+#include "common.cuh"
+
+namespace gcge {
+
+struct SyevWork {
+  double *rot = nullptr;      // 3 * D/2 rotation parameters of one round
+  double *V = nullptr;        // d x d accumulated rotations (column-major, ld = dcap)
+  unsigned *sync = nullptr;   // [0]=barrier count, [1]=barrier generation, [2..4]=rotation counters
+  int *flags = nullptr;       // [0]=barrier timeout, [1]=NaN seen, [2]=sweeps
+  int *h_flags = nullptr;     // pinned mirror of flags
+  int dcap = 0;
+  int coop_grid = 0;          // co-resident CTAs for the cooperative launch
+  int alloc(int d);
+  void free_all();
+};
+
+// A (d x d col-major, lda) is destroyed; w[d] ascending; Q (ldq) eigenvectors.
+// Synchronises the stream.  Returns GCGE_OK / GCGE_ETIMEOUT / GCGE_ENAN / GCGE_ECUDA.
+int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevWork &work,
+         int *sweeps, cudaStream_t st);
+
+}  // namespace gcge

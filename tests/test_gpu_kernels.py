@@ -1,0 +1,263 @@
+"""Parity of each hot-path kernel (through the C ABI) with the FP64 oracle's step.
+
+Sizes span several tiles and ragged tails; FP64 kernels must agree to rounding
+(1e-12 relative), FP32 kernels to the FP32 bound stated per test.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import linalg as L
+from oracle import cg as CG
+from oracle import orth as O
+
+from gpu_util import dev, csr_dev, padded, host, subspace_cos
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    import paper_2111_06552_gb300 as gg
+    assert torch.cuda.is_available()
+    gg.lib()
+    return gg
+
+
+def _ragged_csr(n, seed):
+    """Symmetric random pattern with very uneven rows (1 .. ~60 entries) and an empty row."""
+    rng = np.random.default_rng(seed)
+    A = W.random_sparse_spd(n, 0.02, seed)
+    rows = rng.choice(n, size=max(1, n // 50), replace=False)
+    D = sp.random(n, n, density=0.0, format="lil")
+    for r in rows:
+        cols = rng.choice(n, size=min(n, 60), replace=False)
+        D[r, cols] = rng.uniform(-1, 1, cols.size)
+    A = (A + D.tocsr() + D.tocsr().T).tocsr()
+    A.sort_indices()
+    A = A.tolil()
+    A[n // 3, :] = 0.0            # an empty row (structurally)
+    A = A.tocsr()
+    A.eliminate_zeros()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("k", [1, 3, 10, 17, 20, 40, 100, 130])
+def test_spmm_f64_matches_oracle(g, k):
+    import torch
+    n = 1237
+    A = _ragged_csr(n, k)
+    rng = np.random.default_rng(k)
+    X = rng.standard_normal((n, k))
+    Y0 = rng.standard_normal((n, k))
+    ldx, ldy = k + 3, k + 1
+    rp, ci, val = csr_dev(A)
+    Xd = dev(padded(X, ldx))
+    Yd = dev(padded(Y0, ldy))
+    g.gcge_spmm_f64(n, rp, ci, val, k, 2.0, Xd, ldx, -0.5, Yd, ldy)
+    torch.cuda.synchronize()
+    ref = 2.0 * L.spmm(A, X) - 0.5 * Y0
+    got = host(Yd)[:, :k]
+    assert np.abs(got - ref).max() <= 1e-12 * (np.abs(ref).max() + 1)
+    assert np.isnan(host(Yd)[:, k:]).all()           # padding untouched
+
+
+@pytest.mark.parametrize("k", [2, 20, 40, 100])
+def test_spmm_f32_matches_oracle(g, k):
+    import torch
+    p = W.make_config("q1_160", N=12, seed=1)
+    A = p.A
+    n = p.n
+    X = np.random.default_rng(3).standard_normal((n, k)).astype(np.float32)
+    rp, ci, val = csr_dev(A, f32=True)
+    Xd = dev(X)
+    Yd = torch.zeros((n, k), dtype=torch.float32, device="cuda")
+    g.gcge_spmm_f32(n, rp, ci, val, k, 1.0, Xd, k, 0.0, Yd, k)
+    torch.cuda.synchronize()
+    ref = L.spmm(A.astype(np.float32).astype(np.float64), X.astype(np.float64))
+    scale = abs(A).astype(np.float64) @ np.abs(X.astype(np.float64))
+    assert np.all(np.abs(host(Yd) - ref) <= 2e-6 * scale + 1e-30)
+
+
+@pytest.mark.parametrize("n,m,k", [(1, 1, 1), (1000, 7, 5), (4133, 70, 20), (20011, 150, 33),
+                                   (3001, 200, 100)])
+def test_gram_f64_into_strided_subblock(g, n, m, k):
+    import torch
+    rng = np.random.default_rng(n + m)
+    X = rng.standard_normal((n, m))
+    Y = rng.standard_normal((n, k))
+    ldc, r0, c0 = m + 9, 4, 3
+    Cbig = np.full((ldc, k + 6), 7.0)     # column-major ldc x (k+6) as a (k+6, ldc) C-order array
+    Cd = dev(Cbig.T.copy())
+    base = Cd.data_ptr() + 8 * (r0 + c0 * ldc)
+    g.gcge_gram_f64(n, m, k, 1.5, dev(X), m, dev(Y), k, 0.5, base, ldc)
+    torch.cuda.synchronize()
+    got = host(Cd).T        # ldc x (k+6) column-major view
+    ref = 1.5 * (X.T @ Y) + 0.5 * 7.0
+    assert np.abs(got[r0:r0 + m, c0:c0 + k] - ref).max() <= 1e-12 * (np.abs(ref).max() + 1)
+    mask = np.ones_like(got, dtype=bool)
+    mask[r0:r0 + m, c0:c0 + k] = False
+    assert np.all(got[mask] == 7.0)
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("n,m,k", [(5000, 70, 20), (20011, 150, 33), (65536 + 17, 96, 40)])
+def test_gram_f32(g, n, m, k, tc):
+    import torch
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Y = rng.standard_normal((n, k)).astype(np.float32)
+    Cd = torch.zeros((k, m), dtype=torch.float64, device="cuda")   # col-major m x k
+    g.gcge_gram_f32(n, m, k, 1.0, dev(X), m, dev(Y), k, 0.0, Cd, m, tc=tc)
+    torch.cuda.synchronize()
+    ref = X.astype(np.float64).T @ Y.astype(np.float64)
+    bound = np.abs(X.astype(np.float64)).T @ np.abs(Y.astype(np.float64))
+    assert np.all(np.abs(host(Cd).T - ref) <= 2e-6 * bound)
+
+
+@pytest.mark.parametrize("n,d,q", [(1, 1, 1), (999, 13, 7), (10007, 200, 180), (4096, 70, 50)])
+def test_vc_f64(g, n, d, q):
+    import torch
+    rng = np.random.default_rng(d)
+    V = rng.standard_normal((n, d))
+    Cm = rng.standard_normal((d, q))
+    Y0 = rng.standard_normal((n, q))
+    ldv, ldy, ldc = d + 2, q + 5, d + 1
+    Cbuf = np.zeros((q, ldc))
+    Cbuf[:, :d] = Cm.T                   # column-major d x q with ldc
+    Yd = dev(padded(Y0, ldy))
+    g.gcge_vc_f64(n, d, q, -1.0, dev(padded(V, ldv)), ldv, dev(Cbuf), ldc, 2.0, Yd, ldy)
+    torch.cuda.synchronize()
+    ref = -(V @ Cm) + 2.0 * Y0
+    assert np.abs(host(Yd)[:, :q] - ref).max() <= 1e-12 * (np.abs(ref).max() + 1)
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_vc_f32(g, tc):
+    import torch
+    n, d, q = 33001, 120, 100
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((n, d)).astype(np.float32)
+    Cm = rng.standard_normal((d, q))
+    Yd = torch.zeros((n, q), dtype=torch.float32, device="cuda")
+    g.gcge_vc_f32(n, d, q, 1.0, dev(V), d, dev(Cm.T.copy()), d, 0.0, Yd, q, tc=tc)
+    torch.cuda.synchronize()
+    ref = V.astype(np.float64) @ Cm
+    bound = np.abs(V.astype(np.float64)) @ np.abs(Cm)
+    assert np.all(np.abs(host(Yd) - ref) <= 2e-6 * bound + 1e-6)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 16, 17, 64, 70, 129, 200])
+def test_syev_matches_oracle(g, d):
+    import torch
+    rng = np.random.default_rng(d)
+    M = rng.standard_normal((d, d))
+    M = M + M.T
+    if d >= 16:   # include an exactly repeated eigenvalue and a wide spread
+        Q, _ = np.linalg.qr(rng.standard_normal((d, d)))
+        lam = np.sort(rng.uniform(1, 1e4, d))
+        lam[3:6] = lam[3]
+        M = (Q * lam) @ Q.T
+        M = 0.5 * (M + M.T)
+    w_ref, _ = L.sym_eig(M)
+    Ad = dev(M.T.copy())
+    wd = torch.zeros(d, dtype=torch.float64, device="cuda")
+    Qd = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    sweeps = g.gcge_syev(d, Ad, d, wd, Qd, d)
+    w = host(wd)
+    Qh = host(Qd).T
+    nrm = np.abs(w_ref).max()
+    assert np.abs(w - w_ref).max() <= 1e-13 * nrm * max(1.0, np.sqrt(d) / 4)
+    assert np.abs(Qh.T @ Qh - np.eye(d)).max() <= 1e-13 * d
+    assert np.abs(M @ Qh - Qh * w).max() <= 1e-12 * nrm
+    assert sweeps < 30
+
+
+def test_syev_degenerate_and_diagonal(g):
+    import torch
+    for M in (np.eye(8), np.diag(np.arange(10.0)[::-1]), np.zeros((5, 5))):
+        d = M.shape[0]
+        wd = torch.zeros(d, dtype=torch.float64, device="cuda")
+        Qd = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+        g.gcge_syev(d, dev(M.T.copy()), d, wd, Qd, d)
+        assert np.allclose(host(wd), np.sort(np.diag(M)))
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.7])
+def test_block_cg_matches_oracle(g, theta):
+    import torch
+    p = W.make_config("q1grad_48", N=9, seed=4)
+    n = p.n
+    rng = np.random.default_rng(1)
+    k = 7
+    X0 = rng.standard_normal((n, k))
+    lam = np.linspace(20, 40, k)
+    rhs = L.spmm(p.B, X0) * (lam - theta)
+    S = CG.shifted_matrix(p.A, p.B, theta)
+    for max_iter, rtol in ((4, 0.0), (30, 1e-2)):
+        ref, it_ref, _ = CG.shifted_cg(p.A, p.B, theta, X0, lam, max_iter, rtol, rhs=rhs)
+        rp, ci, val = csr_dev(S)
+        Xd = dev(padded(X0, k + 1))
+        it = g.gcge_block_cg_f64(n, rp, ci, val, k, dev(rhs), k, Xd, k + 1, max_iter, rtol)
+        torch.cuda.synchronize()
+        assert np.array_equal(it, it_ref)
+        got = host(Xd)[:, :k]
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_block_cg_f32(g):
+    import torch
+    p = W.make_config("fd3d_128", N=12, seed=2)
+    n = p.n
+    k = 5
+    X0 = np.random.default_rng(2).standard_normal((n, k))
+    lam = np.full(k, 10.0)
+    rhs = L.spmm(p.B, X0) * lam
+    ref, it_ref, _ = CG.shifted_cg(p.A, p.B, 0.0, X0, lam, 6, 0.0, rhs=rhs)
+    rp, ci, val = csr_dev(p.A, f32=True)
+    Xd = dev(X0.astype(np.float32))
+    it = g.gcge_block_cg_f32(n, rp, ci, val, k, dev(rhs.astype(np.float32)), k, Xd, k, 6, 0.0)
+    torch.cuda.synchronize()
+    assert np.all(it == 6)
+    assert np.abs(host(Xd) - ref).max() <= 2e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("m,q", [(1, 0), (5, 0), (20, 6), (37, 11)])
+def test_borth_matches_oracle(g, m, q):
+    import torch
+    p = W.make_config("q1grad_48", N=8, seed=5)
+    n = p.n
+    rng = np.random.default_rng(m)
+    Q0, _ = O.b_orthonormalize(rng.standard_normal((n, q)), None, p.B) if q else (None, None)
+    X = rng.standard_normal((n, m))
+    if m >= 5:
+        X[:, 3] = X[:, 0] - 2 * X[:, 1]                   # dependent inside the block
+    if q and m >= 5:
+        X[:, 4] = Q0 @ rng.standard_normal(q)             # inside span(Q0)
+    Y_ref, _ = O.b_orthonormalize(X, Q0, p.B)
+    rp, ci, val = csr_dev(p.B)
+    Wd = dev(padded(X, m))
+    Qd = dev(Q0) if q else None
+    mo = g.gcge_borth_f64(n, rp, ci, val, Qd, q if q else 1, q, Wd, m, m, 16)
+    torch.cuda.synchronize()
+    assert mo == Y_ref.shape[1]
+    Y = host(Wd)[:, :mo]
+    BY = p.B @ Y
+    assert np.abs(Y.T @ BY - np.eye(mo)).max() < 1e-12
+    if q:
+        assert np.abs(Q0.T @ BY).max() < 1e-12
+    cos = subspace_cos(Y, Y_ref, p.B)
+    assert cos.min() > 1 - 1e-10
+
+
+def test_random_block_matches_generator(g):
+    import torch
+    n, k = 1001, 13
+    Xd = torch.zeros((n, k + 3), dtype=torch.float64, device="cuda")
+    g.gcge_random_block_f64(n, k, 12345, Xd, k + 3)
+    torch.cuda.synchronize()
+    ref = W.initial_block(n, k, 12345)
+    assert np.abs(host(Xd)[:, :k] - ref).max() < 1e-12
