@@ -29,8 +29,10 @@ Readings where the paper is silent or ambiguous:
 * theta = 0 before the first lock (Remark 3.1 allows 0 <= theta);
 * P is built for the *next* active block (blockSize columns), and the rows
   zeroed are those of the active block X_n that produced W in this iteration;
-* p~ columns whose norm after projection is <= ``p_drop`` are dropped;
-* in moving mode the new window keeps min(3 bs, d - locked) Ritz vectors and
+* p~ directions whose Gram eigenvalue after projection is <= max(1e-14 max,
+  p_drop^2) are dropped (the same relative-plus-floor test as Algorithm 3's leaf);
+* in moving mode the new window keeps min(sizeX, d - locked) Ritz vectors (sizeX =
+  3 bs by default) and
   W is always deflated against the whole store as well;
 * one iteration = one Rayleigh-Ritz solve (the initial one counts as 1).
 """
@@ -75,7 +77,7 @@ def _l2_orthonormal_against(pt: np.ndarray, xh: np.ndarray, drop: float) -> np.n
         if pt.shape[1] == 0:
             return pt
         lam, Q = sym_eig(pt.T @ pt)
-        keep = lam > drop * drop
+        keep = lam > max(1e-14 * float(np.max(lam)), drop * drop)
         pt = pt @ (Q[:, keep] / np.sqrt(lam[keep])[None, :])
     return pt
 
@@ -138,7 +140,7 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
             Xall = Va @ Q
             store = np.hstack([store, X[:, :lw], Xall[:, :c]])
             store_lam = np.concatenate([store_lam, lam[:lw], theta_all[:c]])
-            keep = min(3 * bs, d - c)
+            keep = min(size_x, d - c)
             X = Xall[:, c:c + keep]
             lam = theta_all[c:c + keep].copy()
             lw = 0

@@ -18,8 +18,10 @@ Readings where the paper is silent (collected in ``OrthParams``):
 * "small enough" for a deflation step means max_ij |R_ij| / ||w_j||_B <= tol,
   measured on the block before the subtraction, at most three passes;
 * a column whose B-norm after phase 1 fell below ``drop_tol`` is linearly
-  dependent on Q and is removed; inside a leaf an eigenvalue of M below
-  ``leaf_drop`` marks a dependent direction, which is removed.  Removal
+  dependent on Q and is removed; inside a leaf an eigenvalue of M "close to
+  zero" is one at or below max(leaf_rel * max(Lambda), leaf_drop): relative to
+  the rounding level of the computed Gram M, with an absolute floor for a block
+  whose columns all collapsed; such directions are removed.  Removal
   compacts the block (the paper moves the trailing vectors into the freed
   slots; only the span matters to the Rayleigh-Ritz step);
 * when the column count m is not a power of two the split is at floor(m/2).
@@ -41,6 +43,7 @@ class OrthParams:
     leaf_tol: float = 1e-12
     leaf_max: int = 3
     leaf_drop: float = 1e-20
+    leaf_rel: float = 1e-14
     inner_tol: float = 1e-12
     inner_max: int = 3
     leaf: int = 16
@@ -85,7 +88,7 @@ def _leaf(W: np.ndarray, BW: np.ndarray, p: OrthParams):
             break
         M = W.T @ BW
         lam, Q = sym_eig(M)
-        keep = lam > p.leaf_drop
+        keep = lam > max(p.leaf_rel * float(np.max(lam)), p.leaf_drop)
         C = Q[:, keep] / np.sqrt(lam[keep])[None, :]
         W = W @ C
         BW = BW @ C

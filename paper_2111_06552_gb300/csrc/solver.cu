@@ -47,19 +47,24 @@ void DevCsr::free_all() {
 namespace {
 
 // ------------------------------------------------------------------ small device kernels
-// Keep the eigenpairs of a leaf Gram with lam > thr (ascending order) and form
-// C[:, t] = Q[:, idx_t] / sqrt(lam_t); out_i[0] = kept count, out_d[0] = max |lam_kept - 1|.
+// Keep the eigenpairs of a leaf Gram with lam > max(rel * max(lam), thr) (ascending order)
+// and form C[:, t] = Q[:, idx_t] / sqrt(lam_t); out_i[0] = kept count,
+// out_d[0] = max |lam_kept - 1|.  The relative part follows the rounding level of the
+// computed Gram; the absolute floor catches a block whose columns all collapsed.
 __global__ void leaf_coeffs_kernel(int len, const double *__restrict__ lam,
                                    const double *__restrict__ Q, int64_t ldq, double thr,
-                                   double *__restrict__ C, int64_t ldc, int *__restrict__ out_i,
-                                   double *__restrict__ out_d) {
+                                   double rel, double *__restrict__ C, int64_t ldc,
+                                   int *__restrict__ out_i, double *__restrict__ out_d) {
   __shared__ int idx[1024];
   __shared__ int r;
   if (threadIdx.x == 0) {
+    double lmax = 0.0;
+    for (int i = 0; i < len; ++i) lmax = fmax(lmax, lam[i]);
+    const double cut = fmax(rel * lmax, thr);
     int cnt = 0;
     double mx = 0.0;
     for (int i = 0; i < len; ++i) {
-      if (lam[i] > thr) {
+      if (lam[i] > cut) {
         idx[cnt++] = i;
         mx = fmax(mx, fabs(lam[i] - 1.0));
       }
@@ -227,7 +232,7 @@ int small_grid(int64_t tot) {
 // readings taken: relative deflation size, drop level after unit B-norm scaling,
 // leaf repeat until max|Lambda - 1| small, P-construction drop.
 struct Thresholds {
-  double defl_tol, drop_tol, leaf_tol, leaf_drop, inner_tol, p_drop;
+  double defl_tol, drop_tol, leaf_tol, leaf_drop, inner_tol, p_drop, leaf_rel;
   int defl_max, leaf_max, inner_max;
 };
 
@@ -235,11 +240,11 @@ template <typename T>
 Thresholds thresholds();
 template <>
 Thresholds thresholds<double>() {
-  return {1e-12, 1e-10, 1e-12, 1e-20, 1e-12, 1e-10, 3, 3, 3};
+  return {1e-12, 1e-10, 1e-12, 1e-20, 1e-12, 1e-10, 1e-14, 3, 3, 3};
 }
 template <>
 Thresholds thresholds<float>() {
-  return {1e-5, 1e-4, 1e-5, 1e-8, 1e-5, 1e-5, 3, 3, 3};
+  return {1e-5, 1e-4, 1e-5, 1e-8, 1e-5, 1e-5, 1e-6, 3, 3, 3};
 }
 
 struct QPart {
@@ -569,8 +574,8 @@ int Engine<T>::leaf(T *W, T *BW, int64_t ld, int len, int *out) {
     symmetrize_kernel<<<1, 256, 0, st_>>>(len, 0, Ms_, kLeaf);
     GCGE_LAUNCH_CHECK();
     GCGE_CHECK(syev_small(len, Ms_, kLeaf, Ml_, Mq_, kLeaf));
-    leaf_coeffs_kernel<<<1, 256, 0, st_>>>(len, Ml_, Mq_, kLeaf, th_.leaf_drop, Mc_, kLeaf, d_cnt_,
-                                           d_crit_);
+    leaf_coeffs_kernel<<<1, 256, 0, st_>>>(len, Ml_, Mq_, kLeaf, th_.leaf_drop, th_.leaf_rel, Mc_,
+                                           kLeaf, d_cnt_, d_crit_);
     GCGE_LAUNCH_CHECK();
     g_launches += 2;
     GCGE_CUDA(cudaMemcpyAsync(h_i_, d_cnt_, sizeof(int), cudaMemcpyDeviceToHost, st_));
@@ -809,8 +814,8 @@ int Engine<T>::build_p(int d, int c, int bsn, int *np_out) {
     symmetrize_kernel<<<1, 256, 0, st_>>>(r, 0, Ms_, kLeaf);
     GCGE_LAUNCH_CHECK();
     GCGE_CHECK(syev_small(r, Ms_, kLeaf, Ml_, Mq_, kLeaf));
-    leaf_coeffs_kernel<<<1, 256, 0, st_>>>(r, Ml_, Mq_, kLeaf, th_.p_drop * th_.p_drop, Mc_, kLeaf,
-                                           d_cnt_, d_crit_);
+    leaf_coeffs_kernel<<<1, 256, 0, st_>>>(r, Ml_, Mq_, kLeaf, th_.p_drop * th_.p_drop,
+                                           th_.leaf_rel, Mc_, kLeaf, d_cnt_, d_crit_);
     GCGE_LAUNCH_CHECK();
     g_launches += 3;
     GCGE_CHECK(read_i(d_cnt_, h_i_, 1));

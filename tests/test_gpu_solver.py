@@ -1,9 +1,11 @@
 """End-to-end parity of gcge_solve (through the C ABI) with the FP64 oracle.
 
 Eigenvalues: relative error <= 1e-8 against the oracle and, where one exists,
-the closed form.  Eigenvectors: grouped into clusters of relative gap <= 1e-6
-and compared by principal angles (cos >= 1 - 1e-6 ... i.e. angle <= ~1e-3 rad is
-NOT enough: we require the sine of the largest angle <= 1e-6).
+the closed form.  Eigenvectors: grouped into clusters of relative gap <= 1e-6;
+each computed cluster must lie in the reference eigenspace of that cluster
+(the sine of the largest principal angle <= 1e-6).  For a cluster cut by nev the
+reference is the whole eigenspace, so on small pencils it comes from a dense
+solve of the full problem (test-side only).
 """
 import numpy as np
 import pytest
@@ -26,17 +28,20 @@ def g():
     return gg
 
 
-def _check_vectors(X, Xref, ev, B, full_ref=None):
-    """Largest principal-angle sine per eigenvalue cluster <= 1e-6."""
-    Bm = B
+def _check_vectors(X, ev, A, B):
+    """Largest sine of the principal angles between each computed cluster and the
+    full reference eigenspace of its eigenvalue (dense solve; small pencils only)."""
+    import scipy.linalg as sl
+    Bd = None if B is None else B.toarray()
+    w, V = sl.eigh(A.toarray(), Bd)
     worst = 0.0
     for grp in cluster_groups(ev):
-        Xg = X[:, grp]
-        R = Xref[:, grp] if full_ref is None else full_ref(grp)
-        BR = R if Bm is None else Bm @ R
-        s = np.linalg.svd(Xg.T @ BR, compute_uv=False)
-        # sines of the principal angles (subspace of Xg inside span(R))
-        sin = np.sqrt(np.maximum(0.0, 1.0 - np.min(s) ** 2)) if len(grp) <= R.shape[1] else 1.0
+        lam = ev[grp[0]]
+        ref = np.nonzero(np.abs(w - lam) <= 1e-6 * abs(lam))[0]
+        R = V[:, ref]
+        BR = R if B is None else B @ R
+        s = np.linalg.svd(X[:, grp].T @ BR, compute_uv=False)
+        sin = np.sqrt(max(0.0, 1.0 - float(np.min(s)) ** 2)) if len(grp) <= len(ref) else 1.0
         worst = max(worst, sin)
     return worst
 
@@ -67,7 +72,7 @@ def test_solver_matches_oracle(g, name, N, nev, bs):
     assert res.max() < 1e-8
     Bx = X if p.B is None else p.B @ X
     assert np.abs(X.T @ Bx - np.eye(nev)).max() < 1e-10
-    assert _check_vectors(X, ref.evecs, ev, p.B) <= 1e-6
+    assert _check_vectors(X, ev, p.A, p.B) <= 1e-6
     # the structured Rayleigh-Ritz matrix equals the explicit V^T A V (Eq. struct_bar_A_new)
     assert st["max_abar_err"] <= 1e-8
     assert st["max_orth_err"] <= 1e-10
