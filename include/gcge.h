@@ -243,6 +243,25 @@ int gcge_borth_f64(int64_t n, const int32_t *d_Brp, const int32_t *d_Bci, const 
                    const double *d_Q, int64_t ldq, int q, double *d_W, int64_t ldw, int m,
                    int leaf, int *m_out, void *stream);
 
+/* Gram product without any device allocation (the paper has no counterpart; it
+ * exists for callers that cannot allocate while they run -- e.g. their own allocator
+ * has reserved the GPU's memory, or cudaMalloc/cudaFree's synchronisation is not
+ * acceptable in their loop).  Same arguments and result as gcge_gram_f64, all
+ * pointers device memory.  Its split-K partial sums live in one static device array
+ * of GCGE_GRAM_NOALLOC_MAX_DOUBLES doubles (16 MiB) that every GPU loading the
+ * library holds until exit.
+ *   - m * k must be <= GCGE_GRAM_NOALLOC_MAX_DOUBLES, else GCGE_EINVAL (with a
+ *     message in gcge_last_error_message()); larger m * k uses fewer row splits.
+ *   - The first call on a device looks up the array's device address on that
+ *     device; make that first call before any stream capture.
+ *   - All calls share the one array: calls that may overlap on the GPU (different
+ *     streams, concurrent threads) race and must be serialised by the caller.
+ *   - Calls no cudaMalloc/cudaFree or other allocating routine. */
+#define GCGE_GRAM_NOALLOC_MAX_DOUBLES (2 * 1024 * 1024)
+int gcge_gram_f64_noalloc(int64_t n, int m, int k, double alpha, const double *d_X, int64_t ldx,
+                          const double *d_Y, int64_t ldy, double beta, double *d_C, int64_t ldc,
+                          void *stream);
+
 /* N(0,1) block from the counter-based generator: entry (i, j) of the n x k
  * row-major block (ld) uses counter i*k + j; u1, u2 from
  * splitmix64(splitmix64(seed) + 2c) and (... + 2c + 1), z = sqrt(-2 ln u1) cos(2 pi u2). */

@@ -96,7 +96,9 @@ _SIGS = {
     "gcge_block_cg_f32": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
     "gcge_borth_f64": (_I, [_I64, _P, _P, _P, _P, _I64, _I, _P, _I64, _I, _I, C.POINTER(_I), _P]),
     "gcge_random_block_f64": (_I, [_I64, _I, C.c_uint64, _P, _I64, _P]),
+    "gcge_gram_f64_noalloc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
 }
+GCGE_GRAM_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
 
 
 def lib_path() -> str:
@@ -159,6 +161,13 @@ def gcge_spmm_f32(n, row_ptr, col_idx, val, k, alpha, X, ldx, beta, Y, ldy, stre
 def gcge_gram_f64(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, stream=None):
     return _check(lib().gcge_gram_f64(n, m, k, alpha, _addr(X), ldx, _addr(Y), ldy, beta,
                                       _addr(Cm), ldc, _stream(stream)), "gcge_gram_f64")
+
+
+def gcge_gram_f64_noalloc(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, stream=None):
+    """gcge_gram_f64 without device allocation (static library scratch; see gcge.h)."""
+    return _check(lib().gcge_gram_f64_noalloc(n, m, k, alpha, _addr(X), ldx, _addr(Y), ldy, beta,
+                                              _addr(Cm), ldc, _stream(stream)),
+                  "gcge_gram_f64_noalloc")
 
 
 def gcge_gram_f32(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, tc=1, stream=None):

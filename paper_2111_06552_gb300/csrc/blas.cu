@@ -429,6 +429,37 @@ int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T
   return GCGE_OK;
 }
 
+int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx,
+                       const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                       double *ws, int64_t ws_doubles, cudaStream_t st) {
+  if (m <= 0 || k <= 0) return GCGE_OK;
+  const int64_t mk = (int64_t)m * k;
+  if (mk > ws_doubles) return GCGE_EINVAL;
+  const int tm = ceil_div(m, GM), tk = ceil_div(k, GK);
+  const int64_t tiles = (int64_t)tm * tk;
+  int64_t splits = ((int64_t)device_sm_count() * 4 + tiles - 1) / tiles;
+  const int64_t max_splits = (n + 4 * GR - 1) / (4 * GR);
+  if (splits > max_splits) splits = max_splits;
+  if (splits > ws_doubles / mk) splits = ws_doubles / mk;
+  if (splits > 65535) splits = 65535;
+  if (splits < 1) splits = 1;
+  int64_t rps = round_up((n + splits - 1) / splits, GR);
+  if (rps < GR) rps = GR;
+  splits = (n + rps - 1) / rps;
+  if (splits < 1) splits = 1;
+  if (n > 0) {
+    dim3 grid(tm, tk, (unsigned)splits);
+    gram_partial_kernel<double><<<grid, 256, 0, st>>>(n, m, k, X, ldx, Y, ldy, rps, ws);
+    GCGE_LAUNCH_CHECK();
+  } else {
+    // nothing to reduce: the used partial block must read as zero
+    GCGE_CUDA(cudaMemsetAsync(ws, 0, sizeof(double) * mk, st));
+  }
+  gram_reduce_kernel<<<elem_grid(mk), 256, 0, st>>>(m, k, (int)splits, ws, alpha, beta, C, ldc);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+
 template <typename T>
 int vc_tc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
           int64_t ldc, double beta, T *Y, int64_t ldy, cudaStream_t st);

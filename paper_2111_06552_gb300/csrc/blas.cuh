@@ -20,6 +20,13 @@ template <typename T>
 int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
          double beta, double *C, int64_t ldc, int tc, Scratch &ws, cudaStream_t st);
 
+// Same product as gram() for FP64 blocks, with a caller-owned partial-sum workspace of
+// `ws_doubles` doubles instead of an allocated one (fewer row splits when it is small).
+// Returns GCGE_EINVAL when even one split (m * k doubles) does not fit.
+int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx,
+                       const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                       double *ws, int64_t ws_doubles, cudaStream_t st);
+
 // Y(n x q) = alpha * V(n x d) C(d x q col-major FP64) + beta * Y.
 template <typename T>
 int vc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
