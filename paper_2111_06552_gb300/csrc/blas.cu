@@ -100,6 +100,72 @@ gram_partial_kernel(int64_t n, int m, int k, const T *__restrict__ X, int64_t ld
     }
 }
 
+// FP64 Gram with exact-fit tiles: the FP64 units are the bound on this GPU, so the
+// tile (TMx x TKx <= 64 x 32, chosen per call to cover m and k with little padding)
+// gives every thread up to 8 outputs; output o = t + 256 i sits at (o % TMx, o / TMx).
+template <int O>
+__global__ void __launch_bounds__(256)
+gram64_partial_kernel(int64_t n, int m, int k, int TMx, int TKx, const double *__restrict__ X,
+                      int64_t ldx, const double *__restrict__ Y, int64_t ldy,
+                      int64_t rows_per_split, double *__restrict__ part) {
+  __shared__ double sx[GR][GM + 1];
+  __shared__ double sy[GR][GK + 1];
+  const int m0 = blockIdx.x * TMx, k0 = blockIdx.y * TKx;
+  const int mt = (m - m0) < TMx ? (m - m0) : TMx;
+  const int kt = (k - k0) < TKx ? (k - k0) : TKx;
+  const int nout = mt * kt;
+  const int64_t r0 = (int64_t)blockIdx.z * rows_per_split;
+  int64_t r1 = r0 + rows_per_split;
+  if (r1 > n) r1 = n;
+  int om[O], ok[O];
+  double acc[O];
+#pragma unroll
+  for (int i = 0; i < O; ++i) {
+    const int o = threadIdx.x + 256 * i;
+    om[i] = o < nout ? o % mt : 0;
+    ok[i] = o < nout ? o / mt : 0;
+    acc[i] = 0.0;
+  }
+  for (int64_t rb = r0; rb < r1; rb += GR) {
+    for (int t = threadIdx.x; t < GR * mt; t += 256) {
+      const int rr = t / mt, cc = t % mt;
+      const int64_t r = rb + rr;
+      sx[rr][cc] = r < r1 ? X[r * ldx + m0 + cc] : 0.0;
+    }
+    for (int t = threadIdx.x; t < GR * kt; t += 256) {
+      const int rr = t / kt, cc = t % kt;
+      const int64_t r = rb + rr;
+      sy[rr][cc] = r < r1 ? Y[r * ldy + k0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < GR; ++rr) {
+#pragma unroll
+      for (int i = 0; i < O; ++i) acc[i] += sx[rr][om[i]] * sy[rr][ok[i]];
+    }
+    __syncthreads();
+  }
+  double *pp = part + (int64_t)blockIdx.z * m * k;
+#pragma unroll
+  for (int i = 0; i < O; ++i) {
+    const int o = threadIdx.x + 256 * i;
+    if (o < nout) pp[(int64_t)(k0 + ok[i]) * m + (m0 + om[i])] = acc[i];
+  }
+}
+
+void launch_gram64(dim3 grid, cudaStream_t st, int64_t n, int m, int k, int TMx, int TKx,
+                   const double *X, int64_t ldx, const double *Y, int64_t ldy, int64_t rps,
+                   double *part) {
+  const int O = (TMx * TKx + 255) / 256;
+  switch (O) {
+#define GCGE_G64(o) \
+    case o: gram64_partial_kernel<o><<<grid, 256, 0, st>>>(n, m, k, TMx, TKx, X, ldx, Y, ldy, rps, part); break;
+    GCGE_G64(1) GCGE_G64(2) GCGE_G64(3) GCGE_G64(4) GCGE_G64(5) GCGE_G64(6) GCGE_G64(7)
+    default: gram64_partial_kernel<8><<<grid, 256, 0, st>>>(n, m, k, TMx, TKx, X, ldx, Y, ldy, rps, part);
+#undef GCGE_G64
+  }
+}
+
 __global__ void gram_reduce_kernel(int m, int k, int splits, const double *__restrict__ part,
                                    double alpha, double beta, double *__restrict__ C,
                                    int64_t ldc) {
@@ -299,6 +365,18 @@ __global__ void copy_cols_kernel(int64_t n, int k, const TI *__restrict__ X, int
   }
 }
 
+template <typename TI, typename TO>
+__global__ void add_cols_kernel(int64_t n, int k, const TI *__restrict__ X, int64_t ldx,
+                                TO *__restrict__ Y, int64_t ldy) {
+  const int64_t tot = n * k;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / k;
+    const int j = (int)(t % k);
+    Y[r * ldy + j] += (TO)X[r * ldx + j];
+  }
+}
+
 template <typename T>
 __global__ void axpby_cols_kernel(int64_t n, int k, const double *__restrict__ a,
                                   const T *__restrict__ P, int64_t ldp,
@@ -416,8 +494,15 @@ int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T
   double *part = nullptr;
   GCGE_CHECK(ws.get(sizeof(double) * (size_t)splits * m * k, st, (void **)&part));
   if (n > 0) {
-    dim3 grid(tm, tk, (unsigned)splits);
-    gram_partial_kernel<T><<<grid, 256, 0, st>>>(n, m, k, X, ldx, Y, ldy, rps, part);
+    if (sizeof(T) == 8) {
+      const int TMx = ceil_div(m, tm), TKx = ceil_div(k, tk);
+      dim3 grid(tm, tk, (unsigned)splits);
+      launch_gram64(grid, st, n, m, k, TMx, TKx, (const double *)X, ldx, (const double *)Y, ldy,
+                    rps, part);
+    } else {
+      dim3 grid(tm, tk, (unsigned)splits);
+      gram_partial_kernel<T><<<grid, 256, 0, st>>>(n, m, k, X, ldx, Y, ldy, rps, part);
+    }
     GCGE_LAUNCH_CHECK();
   } else {
     GCGE_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * m * k, st));
@@ -591,6 +676,18 @@ int shifted_values(int64_t nnz_u, const int *mapA, const double *valA, const int
 
 GCGE_INST(double)
 GCGE_INST(float)
+
+template <typename TI, typename TO>
+int add_cols(int64_t n, int k, const TI *X, int64_t ldx, TO *Y, int64_t ldy, cudaStream_t st) {
+  if (n <= 0 || k <= 0) return GCGE_OK;
+  add_cols_kernel<TI, TO><<<elem_grid(n * k), 256, 0, st>>>(n, k, X, ldx, Y, ldy);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+template int add_cols<float, double>(int64_t, int, const float *, int64_t, double *, int64_t,
+                                     cudaStream_t);
+template int add_cols<float, float>(int64_t, int, const float *, int64_t, float *, int64_t,
+                                    cudaStream_t);
 
 template int copy_cols<double, double>(int64_t, int, const double *, int64_t, double *, int64_t,
                                        const double *, cudaStream_t);

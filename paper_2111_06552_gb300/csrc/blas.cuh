@@ -59,6 +59,10 @@ template <typename T>
 int axpby_cols(int64_t n, int k, const double *a, const T *P, int64_t ldp, const double *b,
                const T *Q, int64_t ldq, T *out, int64_t ldo, cudaStream_t st);
 
+// Y[:, 0:k] += X[:, 0:k] (X of type TI added in the precision of Y).
+template <typename TI, typename TO>
+int add_cols(int64_t n, int k, const TI *X, int64_t ldx, TO *Y, int64_t ldy, cudaStream_t st);
+
 // Gather columns: Y[:, t] = X[:, idx[t]] for t < k (device idx).
 template <typename T>
 int gather_cols(int64_t n, int k, const int *idx, const T *X, int64_t ldx, T *Y, int64_t ldy,

@@ -2,15 +2,15 @@
 //
 // All k columns advance together with per-column scalars, which equals k
 // independent CG runs.  One CG step is three kernels:
-//   1. q = S p with the per-column partial dots p^T q fused into the SpMM epilogue;
-//   2. every CTA reduces the p^T q partials in a fixed order (so every CTA
-//      derives bit-identical alpha_j), then x += alpha p, r -= alpha q and the
-//      partial dots r^T r;
-//   3. every CTA reduces r^T r the same way, beta_j = r^T r / (previous), p = r + beta p;
-//      CTA 0 records the new r^T r, the step count and the stop flags.
-// A column stops when ||r|| <= rtol ||r0||, after max_iter steps, or when
-// p^T S p <= 0 (breakdown: S = A - theta B is only SPD on the complement of
-// the locked vectors, Section 3.2); stopped columns take no further updates.
+//   1. q = S p, with the per-column dots p^T q fused into the SpMM epilogue
+//      (finished deterministically by the last CTA into pq[k]);
+//   2. alpha_j = rr_j / pq_j; x += alpha p, r -= alpha q; per-column r^T r
+//      (last CTA: rr_new[k], and the breakdown flags for p^T S p <= 0);
+//   3. beta_j = rr_new_j / rr_j; p = r + beta p (last CTA commits rr, the step
+//      counts and the stop flags ||r|| <= rtol ||r0||).
+// Vector kernels move 16-byte chunks when the blocks are aligned.  A stopped
+// column takes no further updates.  Breakdown: S = A - theta B is only SPD on the
+// complement of the locked vectors (Section 3.2), so p^T S p <= 0 stops a column.
 #include "cg.cuh"
 
 namespace gcge {
@@ -19,155 +19,243 @@ namespace {
 
 constexpr int kCgThreads = 256;
 
-__device__ __forceinline__ void reduce_parts_to_smem(int k, int nparts,
-                                                     const double *__restrict__ part,
-                                                     double *__restrict__ s) {
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double acc = 0.0;
-    for (int b = 0; b < nparts; ++b) acc += part[(int64_t)b * k + j];
-    s[j] = acc;
+// Column-sliced elementwise pass: thread (row slot, chunk); VEC columns per chunk.
+template <int VEC>
+struct Slice {
+  int chunks, rows_per_block, row0, chunk;
+  bool on;
+  __device__ Slice(int k) {
+    chunks = (k + VEC - 1) / VEC;
+    const int cpb = chunks < kCgThreads ? chunks : kCgThreads;
+    rows_per_block = kCgThreads / cpb;
+    row0 = threadIdx.x / cpb;
+    chunk = threadIdx.x % cpb;
+    on = row0 < rows_per_block;
   }
+};
+
+// Per-column sums of a(row, j)^2 style reductions over a block -> part[blockIdx.x * k + j].
+template <int VEC>
+__device__ __forceinline__ void block_cols_to_part(const Slice<VEC> &sl, int k, const double (&acc)[VEC],
+                                                   double *sred, double *part) {
+  // sred: kCgThreads * VEC doubles laid out [row0][chunk*VEC + v] with row stride chunks*VEC
+  const int w = sl.chunks * VEC;
+  if (sl.on)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) sred[sl.row0 * w + sl.chunk * VEC + v] = acc[v];
   __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < sl.rows_per_block; ++r) s += sred[r * w + j];
+    part[(int64_t)blockIdx.x * k + j] = s;
+  }
 }
 
-__global__ void cg_init_kernel(int k, int nparts, const double *__restrict__ part,
-                               double *__restrict__ rr, double *__restrict__ r0,
-                               int *__restrict__ active, int *__restrict__ iters,
-                               int *__restrict__ broke, double rtol) {
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double acc = 0.0;
-    for (int b = 0; b < nparts; ++b) acc += part[(int64_t)b * k + j];
-    rr[j] = acc;
-    const double nr = sqrt(acc);
+template <typename T, int VEC>
+__device__ __forceinline__ void ld_vec(const T *p, T (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (VEC == 2) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+    v[0] = *p;
+  }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void st_vec(T *p, const T (&v)[VEC]) {
+  if constexpr (VEC == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  } else {
+    *p = v[0];
+  }
+}
+
+// rr_j = sum r_j^2 (initial): last CTA writes rr, r0, active, iters, broke.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(kCgThreads)
+cg_init_kernel(int64_t n, int k, const T *__restrict__ r, int64_t ld, double *__restrict__ part,
+               unsigned *__restrict__ ticket, double *__restrict__ rr, double *__restrict__ r0,
+               int *__restrict__ active, int *__restrict__ iters, int *__restrict__ broke,
+               double rtol) {
+  extern __shared__ double sm[];
+  Slice<VEC> sl(k);
+  double acc[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) acc[v] = 0.0;
+  if (sl.on) {
+    for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
+         row += (int64_t)gridDim.x * sl.rows_per_block) {
+      const int j0 = sl.chunk * VEC;
+      if (j0 + VEC <= k) {
+        T rv[VEC];
+        ld_vec<T, VEC>(r + row * ld + j0, rv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[v] += (double)rv[v] * (double)rv[v];
+      } else {
+        for (int v = 0; v < VEC && j0 + v < k; ++v) {
+          const double x = (double)r[row * ld + j0 + v];
+          acc[v] += x * x;
+        }
+      }
+    }
+  }
+  block_cols_to_part<VEC>(sl, k, acc, sm, part);
+  __syncthreads();
+  last_cta_reduce(k, part, ticket, sm, [&](int j, double s) {
+    rr[j] = s;
+    const double nr = sqrt(s);
     r0[j] = nr;
     active[j] = (nr <= rtol * nr) ? 0 : 1;
     iters[j] = 0;
     broke[j] = 0;
-  }
+  });
 }
 
-// x += alpha p, r -= alpha q, partial r^T r.  smem: alpha[k], act[k], red[256].
-template <typename T>
+// x += alpha p, r -= alpha q; partial r^T r; last CTA: rrn and breakdown flags.
+template <typename T, int VEC>
 __global__ void __launch_bounds__(kCgThreads)
-cg_update_kernel(int64_t n, int k, int nparts_a, const double *__restrict__ part_a,
-                 const double *__restrict__ rr, int *__restrict__ active,
-                 int *__restrict__ broke, T *__restrict__ x, int64_t ldx,
-                 const T *__restrict__ p, T *__restrict__ r, const T *__restrict__ q, int64_t ld,
-                 double *__restrict__ part_b) {
+cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *__restrict__ rr,
+                 int *__restrict__ active, int *__restrict__ broke, T *__restrict__ x,
+                 int64_t ldx, const T *__restrict__ p, T *__restrict__ r,
+                 const T *__restrict__ q, int64_t ld, double *__restrict__ part,
+                 unsigned *__restrict__ ticket, double *__restrict__ rrn) {
   extern __shared__ double sm[];
-  double *salpha = sm;               // k
-  double *sred = sm + k;             // kCgThreads
-  int *sact = (int *)(sred + kCgThreads);   // k
-  reduce_parts_to_smem(k, nparts_a, part_a, salpha);   // salpha = p^T q
+  double *salpha = sm;                       // k
+  double *sred = sm + k;                     // kCgThreads * VEC
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    const double pq = salpha[j];
-    int a = active[j];
-    if (a && !(pq > 0.0)) {
-      a = 0;
-      if (blockIdx.x == 0) {
-        active[j] = 0;
-        broke[j] = 1;
-      }
-    }
-    sact[j] = a;
-    salpha[j] = a ? rr[j] / pq : 0.0;
+    const bool a = active[j] && pq[j] > 0.0;
+    salpha[j] = a ? rr[j] / pq[j] : 0.0;
   }
   __syncthreads();
-  const int kc = k < kCgThreads ? k : kCgThreads;
-  const int rpp = kCgThreads / kc;
-  for (int j0 = 0; j0 < k; j0 += kc) {
-    const int jj = threadIdx.x % kc, rr_ = threadIdx.x / kc;
-    const int j = j0 + jj;
-    double acc = 0.0;
-    if (rr_ < rpp && j < k) {
-      const T al = (T)salpha[j];
-      const bool a = sact[j] != 0;
-      for (int64_t row = (int64_t)blockIdx.x * rpp + rr_; row < n; row += (int64_t)gridDim.x * rpp) {
-        T rv = r[row * ld + j];
-        if (a) {
-          x[row * ldx + j] += al * p[row * ld + j];
-          rv -= al * q[row * ld + j];
-          r[row * ld + j] = rv;
+  Slice<VEC> sl(k);
+  double acc[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) acc[v] = 0.0;
+  if (sl.on) {
+    const int j0 = sl.chunk * VEC;
+    T al[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) al[v] = (T)(j0 + v < k ? salpha[j0 + v] : 0.0);
+    const bool full = j0 + VEC <= k;
+    for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
+         row += (int64_t)gridDim.x * sl.rows_per_block) {
+      if (full) {
+        T xv[VEC], pv[VEC], rv[VEC], qv[VEC];
+        ld_vec<T, VEC>(x + row * ldx + j0, xv);
+        ld_vec<T, VEC>(p + row * ld + j0, pv);
+        ld_vec<T, VEC>(r + row * ld + j0, rv);
+        ld_vec<T, VEC>(q + row * ld + j0, qv);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          xv[v] += al[v] * pv[v];
+          rv[v] -= al[v] * qv[v];
+          acc[v] += (double)rv[v] * (double)rv[v];
         }
-        acc += (double)rv * (double)rv;
+        st_vec<T, VEC>(x + row * ldx + j0, xv);
+        st_vec<T, VEC>(r + row * ld + j0, rv);
+      } else {
+        for (int v = 0; v < VEC && j0 + v < k; ++v) {
+          const int j = j0 + v;
+          x[row * ldx + j] += al[v] * p[row * ld + j];
+          const T rv = r[row * ld + j] - al[v] * q[row * ld + j];
+          r[row * ld + j] = rv;
+          acc[v] += (double)rv * (double)rv;
+        }
       }
     }
-    sred[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < kc && j0 + threadIdx.x < k) {
-      double s = 0.0;
-      for (int t = threadIdx.x; t < rpp * kc; t += kc) s += sred[t];
-      part_b[(int64_t)blockIdx.x * k + j0 + threadIdx.x] = s;
-    }
-    __syncthreads();
   }
+  block_cols_to_part<VEC>(sl, k, acc, sred, part);
+  __syncthreads();
+  last_cta_reduce(k, part, ticket, sred, [&](int j, double s) {
+    rrn[j] = s;
+    if (active[j] && !(pq[j] > 0.0)) {
+      active[j] = 0;
+      broke[j] = 1;
+    }
+  });
 }
 
-// beta = rr_new / rr, p = r + beta p for the active columns (rr is read-only here;
-// the commit kernel that follows records rr_new).
-template <typename T>
+// p = r + beta p for active columns; last CTA commits rr = rrn, iters, stop flags.
+template <typename T, int VEC>
 __global__ void __launch_bounds__(kCgThreads)
-cg_pupdate_kernel(int64_t n, int k, int nparts_b, const double *__restrict__ part_b,
-                  const double *__restrict__ rr, const int *__restrict__ active,
-                  T *__restrict__ p, const T *__restrict__ r, int64_t ld) {
+cg_pupdate_kernel(int64_t n, int k, const double *__restrict__ rrn, double *__restrict__ rr,
+                  const double *__restrict__ r0, int *__restrict__ active,
+                  int *__restrict__ iters, T *__restrict__ p, const T *__restrict__ r, int64_t ld,
+                  unsigned *__restrict__ ticket, double rtol) {
   extern __shared__ double sm[];
-  double *sbeta = sm;                 // k
-  int *sact = (int *)(sm + k);        // k
-  reduce_parts_to_smem(k, nparts_b, part_b, sbeta);   // sbeta = rr_new
+  double *sbeta = sm;                        // k
+  int *sact = (int *)(sm + k);               // k
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const int a = active[j];
     sact[j] = a;
-    sbeta[j] = a ? sbeta[j] / rr[j] : 0.0;
+    sbeta[j] = a ? rrn[j] / rr[j] : 0.0;
   }
   __syncthreads();
-  const int kc = k < kCgThreads ? k : kCgThreads;
-  const int rpp = kCgThreads / kc;
-  for (int j0 = 0; j0 < k; j0 += kc) {
-    const int jj = threadIdx.x % kc, rr_ = threadIdx.x / kc;
-    const int j = j0 + jj;
-    if (rr_ < rpp && j < k && sact[j]) {
-      const T be = (T)sbeta[j];
-      for (int64_t row = (int64_t)blockIdx.x * rpp + rr_; row < n; row += (int64_t)gridDim.x * rpp)
-        p[row * ld + j] = r[row * ld + j] + be * p[row * ld + j];
+  Slice<VEC> sl(k);
+  if (sl.on) {
+    const int j0 = sl.chunk * VEC;
+    bool any = false;
+    T be[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      const bool a = j0 + v < k && sact[j0 + v];
+      any |= a;
+      be[v] = (T)(a ? sbeta[j0 + v] : 0.0);
+    }
+    const bool full = j0 + VEC <= k;
+    if (any) {
+      for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
+           row += (int64_t)gridDim.x * sl.rows_per_block) {
+        if (full) {
+          T pv[VEC], rv[VEC];
+          ld_vec<T, VEC>(p + row * ld + j0, pv);
+          ld_vec<T, VEC>(r + row * ld + j0, rv);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v)
+            if (sact[j0 + v]) pv[v] = rv[v] + be[v] * pv[v];
+          st_vec<T, VEC>(p + row * ld + j0, pv);
+        } else {
+          for (int v = 0; v < VEC && j0 + v < k; ++v)
+            if (sact[j0 + v]) p[row * ld + j0 + v] = r[row * ld + j0 + v] + be[v] * p[row * ld + j0 + v];
+        }
+      }
     }
   }
-}
-
-// Commit the per-column state after a step (one small kernel, so that no CTA
-// of the p-update reads rr while another rewrites it).
-__global__ void cg_commit_kernel(int k, int nparts_b, const double *__restrict__ part_b,
-                                 double *__restrict__ rr, const double *__restrict__ r0,
-                                 int *__restrict__ active, int *__restrict__ iters, double rtol) {
+  // commit after every CTA has read rr: the last CTA to arrive does it
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     if (!active[j]) continue;
-    double rn = 0.0;
-    for (int b = 0; b < nparts_b; ++b) rn += part_b[(int64_t)b * k + j];
-    rr[j] = rn;
+    rr[j] = rrn[j];
     iters[j] += 1;
-    if (sqrt(rn) <= rtol * r0[j]) active[j] = 0;
+    if (sqrt(rrn[j]) <= rtol * r0[j]) active[j] = 0;
   }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 int upd_grid(int64_t n, int k) {
-  const int kc = k < kCgThreads ? k : kCgThreads;
-  const int rpp = kCgThreads / kc;
-  int64_t g = (n + (int64_t)rpp * 8 - 1) / ((int64_t)rpp * 8);
-  const int64_t cap = (int64_t)device_sm_count() * 4;
+  const int rpp = kCgThreads / (k < kCgThreads ? k : kCgThreads);
+  int64_t g = (n + (int64_t)rpp * 4 - 1) / ((int64_t)rpp * 4);
+  const int64_t cap = (int64_t)device_sm_count() * 8;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }
 
 template <typename T>
-__global__ void residual_init_kernel(int64_t n, int k, T *__restrict__ r, int64_t ld,
-                                     const T *__restrict__ B, int64_t ldb) {
-  const int64_t tot = n * k;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = t / k;
-    const int j = (int)(t % k);
-    r[row * ld + j] = B[row * ldb + j];
-  }
+bool cg_aligned(const T *x, int64_t ldx, const T *r, int64_t ld) {
+  constexpr int vec = 16 / sizeof(T);
+  return (uintptr_t)x % 16 == 0 && (uintptr_t)r % 16 == 0 && ldx % vec == 0 && ld % vec == 0;
 }
 
 }  // namespace
@@ -177,34 +265,95 @@ int CgWork<T>::alloc(int64_t n, int k) {
   if (n <= ncap && k <= kcap) return GCGE_OK;
   free_all();
   ld = round_up(k, 4);
-  const int nb = spmm_dot_blocks(n, k) > upd_grid(n, k) ? spmm_dot_blocks(n, k) : upd_grid(n, k);
+  // both grids grow with k, so sizing for the largest k covers every later call
+  int nb = spmm_dot_blocks(n, k);
+  if (upd_grid(n, k) > nb) nb = upd_grid(n, k);
   const size_t vb = sizeof(T) * (size_t)n * ld;
   GCGE_CUDA(cudaMalloc(&r, vb));
   GCGE_CUDA(cudaMalloc(&p, vb));
   GCGE_CUDA(cudaMalloc(&q, vb));
   GCGE_CUDA(cudaMalloc(&part_a, sizeof(double) * (size_t)nb * k));
   GCGE_CUDA(cudaMalloc(&part_b, sizeof(double) * (size_t)nb * k));
-  GCGE_CUDA(cudaMalloc(&rr, sizeof(double) * k));
-  GCGE_CUDA(cudaMalloc(&r0, sizeof(double) * k));
-  GCGE_CUDA(cudaMalloc(&active, sizeof(int) * k));
-  GCGE_CUDA(cudaMalloc(&iters, sizeof(int) * k));
-  GCGE_CUDA(cudaMalloc(&broke, sizeof(int) * k));
+  GCGE_CUDA(cudaMalloc(&scal, sizeof(double) * 4 * (size_t)k));
+  GCGE_CUDA(cudaMalloc(&flags, sizeof(int) * 3 * (size_t)k));
+  GCGE_CUDA(cudaMalloc(&tickets, sizeof(unsigned) * 4));
+  GCGE_CUDA(cudaMemset(tickets, 0, sizeof(unsigned) * 4));
   GCGE_CUDA(cudaMallocHost(&h_active, sizeof(int) * k));
+  rr = scal;
+  r0 = scal + k;
+  pq = scal + 2 * k;
+  rrn = scal + 3 * k;
+  active = flags;
+  iters = flags + k;
+  broke = flags + 2 * k;
   ncap = n;
   kcap = k;
+  nbcap = nb;
   return GCGE_OK;
 }
 
 template <typename T>
 void CgWork<T>::free_all() {
   cudaFree(r); cudaFree(p); cudaFree(q); cudaFree(part_a); cudaFree(part_b);
-  cudaFree(rr); cudaFree(r0); cudaFree(active); cudaFree(iters); cudaFree(broke);
+  cudaFree(scal); cudaFree(flags); cudaFree(tickets);
   if (h_active) cudaFreeHost(h_active);
   r = p = q = nullptr;
-  part_a = part_b = rr = r0 = nullptr;
-  active = iters = broke = h_active = nullptr;
+  part_a = part_b = scal = rr = r0 = pq = rrn = nullptr;
+  flags = active = iters = broke = h_active = nullptr;
+  tickets = nullptr;
   ncap = 0;
   kcap = 0;
+}
+
+template <typename T, int VEC>
+static int cg_loop(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
+                   T *X, int64_t ldx, int max_iter, double rtol, CgWork<T> &w, int64_t &nl,
+                   cudaStream_t st, KProf *prof, double spmm_bytes, double nnzS) {
+  const int64_t ld = w.ld;
+  const int nbb = upd_grid(n, k);
+  if (nbb > w.nbcap || k > w.kcap) return GCGE_EINVAL;
+  const int chunks = (k + VEC - 1) / VEC;
+  const size_t sm_r = sizeof(double) * (size_t)kCgThreads * VEC + 64;
+  const size_t sm_u = sizeof(double) * ((size_t)k + (size_t)kCgThreads * VEC) + 64;
+  const size_t sm_p = (sizeof(double) + sizeof(int)) * (size_t)k + 64;
+  (void)chunks;
+  const double ts = sizeof(T), nk = (double)n * k;
+  {
+    ProfScope ps(prof, GCGE_K_CGVEC, nk * ts, 2.0 * nk);
+    cg_init_kernel<T, VEC><<<nbb, kCgThreads, sm_r, st>>>(n, k, w.r, ld, w.part_b, w.tickets + 1,
+                                                          w.rr, w.r0, w.active, w.iters, w.broke,
+                                                          rtol);
+    GCGE_LAUNCH_CHECK();
+    ++nl;
+  }
+  for (int it = 0; it < max_iter; ++it) {
+    {
+      ProfScope ps(prof, GCGE_K_SPMM, spmm_bytes, 2.0 * nnzS * k);
+      GCGE_CHECK(launch_spmm<T>(n, rp, ci, S, k, T(1), w.p, ld, T(0), w.q, ld, w.pq, w.nbcap, st,
+                                w.part_a, w.tickets));
+    }
+    {
+      ProfScope ps(prof, GCGE_K_CGVEC, 9.0 * nk * ts, 6.0 * nk);
+      cg_update_kernel<T, VEC><<<nbb, kCgThreads, sm_u, st>>>(n, k, w.pq, w.rr, w.active, w.broke,
+                                                              X, ldx, w.p, w.r, w.q, ld, w.part_b,
+                                                              w.tickets + 2, w.rrn);
+      GCGE_LAUNCH_CHECK();
+      cg_pupdate_kernel<T, VEC><<<nbb, kCgThreads, sm_p, st>>>(n, k, w.rrn, w.rr, w.r0, w.active,
+                                                               w.iters, w.p, w.r, ld,
+                                                               w.tickets + 3, rtol);
+      GCGE_LAUNCH_CHECK();
+    }
+    nl += 3;
+    // poll the stop flags every few steps (one small device->host copy)
+    if ((it % 5) == 4 && it + 1 < max_iter) {
+      GCGE_CUDA(cudaMemcpyAsync(w.h_active, w.active, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+      GCGE_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int j = 0; j < k; ++j) any |= (w.h_active[j] != 0);
+      if (!any) break;
+    }
+  }
+  return GCGE_OK;
 }
 
 template <typename T>
@@ -213,19 +362,13 @@ int block_cg(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
              double rtol, CgWork<T> &w, int *iters_host, int64_t *launches, cudaStream_t st,
              KProf *prof) {
   if (k <= 0 || n <= 0) return GCGE_OK;
-  int64_t nnzS = 0;
-  if (prof) {
-    int32_t last = 0;
-    cudaMemcpy(&last, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    nnzS = last;
-  }
-  const double ts = sizeof(T), nk = (double)n * k;
-  const double spmm_bytes = nnzS * (ts + 4.0) + 4.0 * (n + 1) + 2.0 * nk * ts;
   GCGE_CHECK(w.alloc(n, k));
   const int64_t ld = w.ld;
-  const int nba = spmm_dot_blocks(n, k);
-  const int nbb = upd_grid(n, k);
   int64_t nl = 0;
+  int32_t nnz_last = 0;
+  if (prof) GCGE_CUDA(cudaMemcpy(&nnz_last, rp + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  const double ts = sizeof(T), nk = (double)n * k;
+  const double spmm_bytes = nnz_last * (ts + 4.0) + 4.0 * (n + 1) + 2.0 * nk * ts;
   // r = r_init, or r = B - S X
   if (r_init) {
     GCGE_CHECK(copy_cols<T, T>(n, k, r_init, ldr, w.r, ld, nullptr, st));
@@ -234,52 +377,15 @@ int block_cg(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
     GCGE_CHECK(launch_spmm<T>(n, rp, ci, S, k, T(-1), X, ldx, T(1), w.r, ld, nullptr, 0, st));
     ++nl;
   }
-  ++nl;
   GCGE_CHECK(copy_cols<T, T>(n, k, w.r, ld, w.p, ld, nullptr, st));
-  ++nl;
-  {
-    // initial r^T r: the update kernel with every column marked inactive (alpha = 0)
-    // only reduces r^T r into part_b; cg_init then sets rr, r0 and the flags.
-    const size_t sm = sizeof(double) * (k + kCgThreads) + sizeof(int) * k;
-    GCGE_CUDA(cudaMemsetAsync(w.active, 0, sizeof(int) * k, st));
-    GCGE_CUDA(cudaMemsetAsync(w.part_a, 0, sizeof(double) * (size_t)nba * k, st));
-    cg_update_kernel<T><<<nbb, kCgThreads, sm, st>>>(n, k, nba, w.part_a, w.rr, w.active, w.broke,
-                                                     X, ldx, w.p, w.r, w.q, ld, w.part_b);
-    GCGE_LAUNCH_CHECK();
-    cg_init_kernel<<<1, 256, 0, st>>>(k, nbb, w.part_b, w.rr, w.r0, w.active, w.iters, w.broke,
-                                      rtol);
-    GCGE_LAUNCH_CHECK();
-    nl += 2;
-  }
-  const size_t sm_u = sizeof(double) * (k + kCgThreads) + sizeof(int) * k;
-  const size_t sm_p = sizeof(double) * k + sizeof(int) * k;
-  for (int it = 0; it < max_iter; ++it) {
-    {
-      ProfScope ps(prof, GCGE_K_SPMM, spmm_bytes, 2.0 * nnzS * k);
-      GCGE_CHECK(launch_spmm<T>(n, rp, ci, S, k, T(1), w.p, ld, T(0), w.q, ld, w.part_a, nba, st));
-    }
-    {
-      ProfScope ps(prof, GCGE_K_CGVEC, 9.0 * nk * ts, 6.0 * nk);
-      cg_update_kernel<T><<<nbb, kCgThreads, sm_u, st>>>(n, k, nba, w.part_a, w.rr, w.active,
-                                                         w.broke, X, ldx, w.p, w.r, w.q, ld,
-                                                         w.part_b);
-      GCGE_LAUNCH_CHECK();
-      cg_pupdate_kernel<T><<<nbb, kCgThreads, sm_p, st>>>(n, k, nbb, w.part_b, w.rr, w.active,
-                                                          w.p, w.r, ld);
-      GCGE_LAUNCH_CHECK();
-      cg_commit_kernel<<<1, 256, 0, st>>>(k, nbb, w.part_b, w.rr, w.r0, w.active, w.iters, rtol);
-      GCGE_LAUNCH_CHECK();
-    }
-    nl += 4;
-    // poll the stop flags every few steps (one small device->host copy)
-    if ((it % 4) == 3 && it + 1 < max_iter) {
-      GCGE_CUDA(cudaMemcpyAsync(w.h_active, w.active, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
-      GCGE_CUDA(cudaStreamSynchronize(st));
-      bool any = false;
-      for (int j = 0; j < k; ++j) any |= (w.h_active[j] != 0);
-      if (!any) break;
-    }
-  }
+  nl += 2;
+  constexpr int vmax = 16 / sizeof(T);
+  if (cg_aligned<T>(X, ldx, w.r, ld))
+    GCGE_CHECK(cg_loop<T, vmax>(n, rp, ci, S, k, X, ldx, max_iter, rtol, w, nl, st, prof,
+                                spmm_bytes, nnz_last));
+  else
+    GCGE_CHECK(cg_loop<T, 1>(n, rp, ci, S, k, X, ldx, max_iter, rtol, w, nl, st, prof, spmm_bytes,
+                             nnz_last));
   int mx = 0;
   if (iters_host) {
     GCGE_CUDA(cudaMemcpyAsync(iters_host, w.iters, sizeof(int) * k, cudaMemcpyDeviceToHost, st));

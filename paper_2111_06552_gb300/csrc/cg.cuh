@@ -11,12 +11,15 @@ template <typename T>
 struct CgWork {
   T *r = nullptr, *p = nullptr, *q = nullptr;   // n x ld each
   int64_t ld = 0;
-  double *part_a = nullptr;   // SpMM dot partials  (spmm blocks x k)
-  double *part_b = nullptr;   // update dot partials (update blocks x k)
-  double *rr = nullptr, *r0 = nullptr;          // k each
-  int *active = nullptr, *iters = nullptr, *broke = nullptr;   // k each
+  double *part_a = nullptr;   // SpMM dot partials  (nbcap x k)
+  double *part_b = nullptr;   // vector-kernel partials (nbcap x k)
+  double *scal = nullptr;     // 4k: rr, r0, pq, rrn
+  double *rr = nullptr, *r0 = nullptr, *pq = nullptr, *rrn = nullptr;
+  int *flags = nullptr;       // 3k: active, iters, broke
+  int *active = nullptr, *iters = nullptr, *broke = nullptr;
+  unsigned *tickets = nullptr;   // last-CTA tickets of the reductions (kept at zero)
   int *h_active = nullptr;    // pinned host mirror (k)
-  int kcap = 0;
+  int kcap = 0, nbcap = 0;
   int64_t ncap = 0;
   int alloc(int64_t n, int k);
   void free_all();

@@ -79,4 +79,39 @@ __device__ __forceinline__ T block_sum(T v, T *sh) {
   return r;
 }
 
+// Deterministic cross-CTA finish of per-CTA partial rows part[b * k + j] (b < gridDim.x):
+// every CTA calls this after writing its row; the last CTA to arrive (atomic ticket, left
+// at zero afterwards) sums the rows in a fixed order with all of its threads and calls
+// fin(j, sum) for each column.  `sh` needs blockDim.x doubles.  Returns true in the last CTA.
+template <typename F>
+__device__ __forceinline__ bool last_cta_reduce(int k, const double *part, unsigned *ticket,
+                                                double *sh, F fin) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const int nb = gridDim.x;
+  for (int j0 = 0; j0 < k; j0 += blockDim.x) {
+    const int kc = (k - j0) < (int)blockDim.x ? (k - j0) : (int)blockDim.x;
+    const int slots = blockDim.x / kc;
+    const int slot = threadIdx.x / kc, j = j0 + threadIdx.x % kc;
+    double s = 0.0;
+    if (slot < slots)
+      for (int b = slot; b < nb; b += slots) s += __ldcg(part + (int64_t)b * k + j);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < kc) {
+      double t = 0.0;
+      for (int q = 0; q < slots; ++q) t += sh[q * kc + threadIdx.x];
+      fin(j0 + threadIdx.x, t);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
 }  // namespace gcge

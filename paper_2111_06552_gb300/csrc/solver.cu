@@ -284,7 +284,7 @@ class Engine {
   }
   ~Engine() { free_all(); }
 
-  int setup(int size_x, int nev, int store_cap);
+  int setup(int size_x, int nev, int store_cap, int bs = 0);
   // Start block: device FP64 (X0d) or FP32 (X0f) n x size_x; both null = generator.
   int run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0f);
   // STEP 2 on a caller block (the C ABI's standalone orthogonalisation).
@@ -309,6 +309,8 @@ class Engine {
   bool stagnated = false;
   int stagnation_limit = 0;   // > 0: stop after this many iterations without a new lock
   KProf *prof = nullptr;      // per-kernel-class event profile (null: off)
+  bool cg_fp32 = false;       // FP64 engine: run the inner CG in FP32 on the FP64 residual
+  bool use_p = true;          // build P (STEP 5); the refinement phase may go without it
 
  private:
   gcge_handle *h_;
@@ -355,6 +357,9 @@ class Engine {
   Scratch ws_;
   SyevWork sw_;
   CgWork<T> cg_;
+  CgWork<float> cg32_;
+  float *Sval32_ = nullptr, *R032_ = nullptr, *D32_ = nullptr;   // FP32 inner-CG buffers
+  double theta32_cur_ = -1.0;
   // iteration state
   int off_ = 0, kx_ = 0, np_ = 0, nw_ = 0, nb_old_ = 0, lw_ = 0;
   int nlock_ = 0, it_ = 0;
@@ -452,7 +457,8 @@ int Engine<float>::use_tc() const { return 1; }
 template <typename T>
 void Engine<T>::free_all() {
   if (st_) cudaStreamSynchronize(st_);
-  void *ptrs[] = {V_[0], V_[1], store_, AW_,   R0_,  BWb_,    TMP_,    TMP2_,  AXc_,  BXc_,
+  void *ptrs[] = {Sval32_, R032_, D32_,
+                  V_[0], V_[1], store_, AW_,   R0_,  BWb_,    TMP_,    TMP2_,  AXc_,  BXc_,
                   Sval_, Abar_, Asave_, Qe_,   ph_,  t1_,     t2_,     theta_, lam_,  a0_,
                   Rg_,   Ms_,   Ml_,    Mq_,   Mc_,  d_norm2_, d_scale_, d_res_, d_crit_,
                   d_lamn_, d_m1_, d_idx_, d_cnt_};
@@ -462,6 +468,8 @@ void Engine<T>::free_all() {
   Abar_ = Asave_ = Qe_ = ph_ = t1_ = t2_ = theta_ = lam_ = a0_ = Rg_ = nullptr;
   Ms_ = Ml_ = Mq_ = Mc_ = d_norm2_ = d_scale_ = d_res_ = d_crit_ = d_lamn_ = d_m1_ = nullptr;
   d_idx_ = d_cnt_ = nullptr;
+  Sval32_ = R032_ = D32_ = nullptr;
+  cg32_.free_all();
   if (h_d_) cudaFreeHost(h_d_);
   if (h_i_) cudaFreeHost(h_i_);
   h_d_ = nullptr;
@@ -473,10 +481,10 @@ void Engine<T>::free_all() {
 }
 
 template <typename T>
-int Engine<T>::setup(int size_x, int nev, int store_cap) {
+int Engine<T>::setup(int size_x, int nev, int store_cap, int bs) {
   n_ = h_->n;
   nev_ = nev;
-  bs_ = h_->bs;
+  bs_ = bs > 0 ? bs : h_->bs;
   sizeX_ = size_x;
   dmax_ = sizeX_ + 2 * bs_;
   ldV_ = round_up(dmax_, 4);
@@ -526,7 +534,14 @@ int Engine<T>::setup(int size_x, int nev, int store_cap) {
   GCGE_CUDA(cudaMallocHost(&h_d_, sizeof(double) * (2 * ldC_ + 8)));
   GCGE_CUDA(cudaMallocHost(&h_i_, sizeof(int) * (ldB_ + 8)));
   GCGE_CHECK(sw_.alloc(std::max(dmax_, kLeaf)));
-  GCGE_CHECK(cg_.alloc(n_, bs_));
+  if (cg_fp32 && sizeof(T) == 8) {
+    GCGE_CHECK(alloc_dev((void **)&Sval32_, sizeof(float) * (size_t)h_->S.nnz));
+    GCGE_CHECK(alloc_dev((void **)&R032_, sizeof(float) * n * ldB_));
+    GCGE_CHECK(alloc_dev((void **)&D32_, sizeof(float) * n * ldB_));
+    GCGE_CHECK(cg32_.alloc(n_, bs_));
+  } else {
+    GCGE_CHECK(cg_.alloc(n_, bs_));
+  }
   tm_.init();
   std::vector<double> m1(ldB_, -1.0);
   GCGE_CUDA(cudaMemcpyAsync(d_m1_, m1.data(), sizeof(double) * ldB_, cudaMemcpyHostToDevice, st_));
@@ -854,8 +869,29 @@ int Engine<T>::shifted_cg(const T *Xn, int64_t ldx, int bsn, const T *AXn, int64
   g_launches += 1;
   GCGE_CHECK(axpby_cols<T>(n_, bsn, d_lamn_, BXn, ldb, d_m1_, AXn, lda, R0_, ldB_, st_));
   int64_t nl = 0;
-  const int mx = block_cg<T>(n_, h_->S.rp, h_->S.ci, Sval_, bsn, nullptr, 0, R0_, ldB_, Wout, ldw,
-                             h_->opt.cg_max_iter, h_->opt.cg_rtol, cg_, h_i_, &nl, st_, prof);
+  int mx;
+  if (cg_fp32 && sizeof(T) == 8) {
+    // inexact inner solve in FP32: S delta = r0 from delta = 0, then W = X_n + delta (FP64)
+    if (theta != theta32_cur_) {
+      g_launches += 1;
+      GCGE_CHECK(shifted_values<float>(h_->S.nnz, h_->mapA, h_->A.v64, bI_ ? nullptr : h_->mapB,
+                                       bI_ ? nullptr : h_->B.v64, h_->isdiag, theta, Sval32_,
+                                       st_));
+      theta32_cur_ = theta;
+    }
+    g_launches += 2;
+    GCGE_CHECK(copy_cols<T, float>(n_, bsn, R0_, ldB_, R032_, ldB_, nullptr, st_));
+    GCGE_CUDA(cudaMemsetAsync(D32_, 0, sizeof(float) * (size_t)n_ * ldB_, st_));
+    mx = block_cg<float>(n_, h_->S.rp, h_->S.ci, Sval32_, bsn, nullptr, 0, R032_, ldB_, D32_,
+                         ldB_, h_->opt.cg_max_iter, h_->opt.cg_rtol, cg32_, h_i_, &nl, st_, prof);
+    if (mx >= 0) {
+      g_launches += 1;
+      GCGE_CHECK(add_cols<float, T>(n_, bsn, D32_, ldB_, Wout, ldw, st_));
+    }
+  } else {
+    mx = block_cg<T>(n_, h_->S.rp, h_->S.ci, Sval_, bsn, nullptr, 0, R0_, ldB_, Wout, ldw,
+                     h_->opt.cg_max_iter, h_->opt.cg_rtol, cg_, h_i_, &nl, st_, prof);
+  }
   g_launches += nl;
   if (mx < 0) return mx;
   cg_steps += mx;
@@ -954,7 +990,7 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     }
     const int bsn = std::min(std::min(bs_, nev_ - nlock_), kxn);
     // ---- STEP 5: P from the Ritz block (none right after a move or the first RR)
-    if (!move && !first && nb_old_ > 0 && bsn > 0) {
+    if (use_p && !move && !first && nb_old_ > 0 && bsn > 0) {
       GCGE_CHECK(build_p(d, c, bsn, &npn));
       if (npn > 0) GCGE_CHECK(vcT(d, npn, 1.0, Va, ldV_, ph_, dmax_, 0.0, V_[nxt] + kx_, ldV_));
     }
@@ -1129,10 +1165,14 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
   *iters32 = it1;
   int s;
   {
+    // phase 2: every unconverged column is active at once (block size nev) and the
+    // inexact inner CG runs in FP32 on the FP64 residual
     Engine<double> e2(h, h->tol, std::max(1, h->opt.max_iter - it1));
     e2.checks = h->opt.checks != 0;
+    e2.cg_fp32 = true;
+    e2.use_p = false;
     if (h->opt.profile) e2.prof = &prof;
-    s = e2.setup(sx, h->nev, h->store_cap);
+    s = e2.setup(sx, h->nev, h->store_cap, std::min(h->nev, sx));
     if (s == GCGE_OK) s = e2.run(nullptr, 0, X1, sx);
     *iters = it1 + e2.iterations();
     add_stats(h, e2);

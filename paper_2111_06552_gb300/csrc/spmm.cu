@@ -1,12 +1,20 @@
 // CSR x row-major multivector product, Y = alpha A X + beta Y (MatDotMultiVec, Section 3.4).
 //
 // Layout: X and Y are row-major n x k (ld >= k), so every nonzero a_ij of row i
-// gathers the contiguous k-vector X[j, 0:k].  A group of G lanes (G = the
-// smallest power of two >= k, at most a warp) owns one row at a time; lane l
-// accumulates columns l, l+G, l+2G, ... in registers.  The column index and value
-// of a nonzero are the same address for the whole group (one broadcast
-// transaction); the gathered k-vector is one coalesced segment.  The nonzero
-// loop is unrolled by four so four independent gathers are in flight per lane.
+// gathers the contiguous k-vector X[j, 0:k].  The k columns are cut into 16-byte
+// chunks (4 floats or 2 doubles) when the block is 16-byte aligned, else into single
+// elements.  A group of G lanes owns one row; lane l of the group holds chunks
+// l, l+G, ... (at most NV of them) in registers, so for the block widths of the
+// method (k = 2..100) a row needs 1..8 lanes and a warp works on 4..32 rows at once.
+// This keeps the per-nonzero instruction overhead (index, value, address) shared by
+// a whole row's worth of FMAs and keeps many independent gathers in flight; the
+// nonzero loop is unrolled by four.
+//
+// Optional fused epilogue (used by the CG step): per column j the dot product
+// sum_i X[i, j] (A X)[i, j].  Lanes holding the same columns reduce over the rows of
+// the warp with shuffles, then over the CTA in shared memory; every CTA writes one
+// partial row and the last CTA to finish (atomic ticket) sums the partials in a
+// fixed order into dot_out[0:k], so the result is deterministic.
 #include "spmm.cuh"
 
 namespace gcge {
@@ -15,147 +23,241 @@ namespace {
 
 constexpr int kSpmmThreads = 256;
 
-template <typename T, int G, int C, bool DOT>
+template <typename T, int VEC>
+struct VecT;
+template <>
+struct VecT<float, 4> { using type = float4; };
+template <>
+struct VecT<double, 2> { using type = double2; };
+template <typename T>
+struct VecT<T, 1> { using type = T; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_chunk(const T *p, T (&v)[VEC]) {
+  if constexpr (VEC == 1) {
+    v[0] = __ldg(p);
+  } else {
+    using V = typename VecT<T, VEC>::type;
+    const V t = __ldg(reinterpret_cast<const V *>(p));
+    if constexpr (VEC == 4) {
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      v[0] = t.x; v[1] = t.y;
+    }
+  }
+}
+
+template <typename T, int VEC, int NV, bool DOT>
 __global__ void __launch_bounds__(kSpmmThreads)
 spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-            const T *__restrict__ val, int k, T alpha, const T *__restrict__ X, int64_t ldx,
-            T beta, T *__restrict__ Y, int64_t ldy, double *__restrict__ dot_out) {
-  extern __shared__ double sdot[];
+            const T *__restrict__ val, int k, int G, T alpha, const T *__restrict__ X,
+            int64_t ldx, T beta, T *__restrict__ Y, int64_t ldy, double *__restrict__ part,
+            double *__restrict__ dot_out, unsigned *__restrict__ ticket) {
+  extern __shared__ double sdot[];   // k column sums, then blockDim.x reduction scratch
+  const int nchunks = (k + VEC - 1) / VEC;
+  const int full = k / VEC;                 // chunks that are complete
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (G - 1);            // lane within the row group
   if (DOT) {
     for (int j = threadIdx.x; j < k; j += blockDim.x) sdot[j] = 0.0;
     __syncthreads();
   }
-  const int lane = threadIdx.x & (G - 1);
-  const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const int64_t ngr = ((int64_t)gridDim.x * blockDim.x) / G;
-  double dacc[C];
+  const int64_t rows_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+       row - (threadIdx.x / G) < n; row += rows_per_grid) {
+    T acc[NV][VEC];
 #pragma unroll
-  for (int u = 0; u < C; ++u) dacc[u] = 0.0;
-
-  for (int64_t row = gid; row < n; row += ngr) {
-    const int beg = __ldg(rp + row), end = __ldg(rp + row + 1);
-    for (int j0 = 0; j0 < k; j0 += G * C) {
-      T acc[C];
+    for (int c = 0; c < NV; ++c)
 #pragma unroll
-      for (int u = 0; u < C; ++u) acc[u] = T(0);
-      const int jl = j0 + lane;
+      for (int v = 0; v < VEC; ++v) acc[c][v] = T(0);
+    const bool live = row < n;
+    if (live) {
+      const int beg = __ldg(rp + row), end = __ldg(rp + row + 1);
       int e = beg;
       for (; e + 3 < end; e += 4) {
-        const int c0 = __ldg(ci + e), c1 = __ldg(ci + e + 1), c2 = __ldg(ci + e + 2),
-                  c3 = __ldg(ci + e + 3);
-        const T v0 = __ldg(val + e), v1 = __ldg(val + e + 1), v2 = __ldg(val + e + 2),
-                v3 = __ldg(val + e + 3);
-        const T *x0 = X + (int64_t)c0 * ldx + jl;
-        const T *x1 = X + (int64_t)c1 * ldx + jl;
-        const T *x2 = X + (int64_t)c2 * ldx + jl;
-        const T *x3 = X + (int64_t)c3 * ldx + jl;
+        int cc[4];
+        T vv[4];
 #pragma unroll
-        for (int u = 0; u < C; ++u) {
-          if (jl + u * G < k) {
-            const T a0 = __ldg(x0 + u * G), a1 = __ldg(x1 + u * G), a2 = __ldg(x2 + u * G),
-                    a3 = __ldg(x3 + u * G);
-            acc[u] += v0 * a0;
-            acc[u] += v1 * a1;
-            acc[u] += v2 * a2;
-            acc[u] += v3 * a3;
+        for (int u = 0; u < 4; ++u) {
+          cc[u] = __ldg(ci + e + u);
+          vv[u] = __ldg(val + e + u);
+        }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const int ch = gl + c * G;
+          if (ch < full) {
+            T xv[4][VEC];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              load_chunk<T, VEC>(X + (int64_t)cc[u] * ldx + ch * VEC, xv[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) acc[c][v] += vv[u] * xv[u][v];
+          } else if (ch < nchunks) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              for (int v = 0; v < VEC && ch * VEC + v < k; ++v)
+                acc[c][v] += vv[u] * __ldg(X + (int64_t)cc[u] * ldx + ch * VEC + v);
           }
         }
       }
       for (; e < end; ++e) {
         const int c0 = __ldg(ci + e);
         const T v0 = __ldg(val + e);
-        const T *x0 = X + (int64_t)c0 * ldx + jl;
+        const T *xr = X + (int64_t)c0 * ldx;
 #pragma unroll
-        for (int u = 0; u < C; ++u)
-          if (jl + u * G < k) acc[u] += v0 * __ldg(x0 + u * G);
+        for (int c = 0; c < NV; ++c) {
+          const int ch = gl + c * G;
+          if (ch < full) {
+            T xv[VEC];
+            load_chunk<T, VEC>(xr + ch * VEC, xv);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[c][v] += v0 * xv[v];
+          } else if (ch < nchunks) {
+            for (int v = 0; v < VEC && ch * VEC + v < k; ++v) acc[c][v] += v0 * __ldg(xr + ch * VEC + v);
+          }
+        }
       }
+      // epilogue: Y = alpha acc + beta Y
 #pragma unroll
-      for (int u = 0; u < C; ++u) {
-        const int j = jl + u * G;
-        if (j < k) {
-          T out = alpha * acc[u];
-          T *yp = Y + row * ldy + j;
-          if (beta != T(0)) out += beta * *yp;
-          *yp = out;
-          if (DOT) dacc[u] += (double)X[row * ldx + j] * (double)acc[u];
+      for (int c = 0; c < NV; ++c) {
+        const int ch = gl + c * G;
+        if (ch >= nchunks) continue;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const int j = ch * VEC + v;
+          if (j < k) {
+            T *yp = Y + row * ldy + j;
+            T out = alpha * acc[c][v];
+            if (beta != T(0)) out += beta * *yp;
+            *yp = out;
+          }
+        }
+      }
+    }
+    if (DOT) {
+      // per column: X[row, j] * (A X)[row, j], reduced over the warp's rows by shuffles
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const int ch = gl + c * G;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const int j = ch * VEC + v;
+          double d = 0.0;
+          if (live && ch < nchunks && j < k) d = (double)X[row * ldx + j] * (double)acc[c][v];
+          for (int o = G; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+          if (lane < G && ch < nchunks && j < k && d != 0.0) atomicAdd(&sdot[j], d);
         }
       }
     }
   }
   if (DOT) {
-#pragma unroll
-    for (int u = 0; u < C; ++u) {
-      const int j = lane + u * G;
-      if (j < k && dacc[u] != 0.0) atomicAdd(&sdot[j], dacc[u]);
-    }
     __syncthreads();
-    for (int j = threadIdx.x; j < k; j += blockDim.x) dot_out[(int64_t)blockIdx.x * k + j] = sdot[j];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) part[(int64_t)blockIdx.x * k + j] = sdot[j];
+    last_cta_reduce(k, part, ticket, sdot + k, [&](int j, double v) { dot_out[j] = v; });
   }
 }
 
-template <typename T, int G, int C>
-void launch_gc(int grid, int64_t n, const int32_t *rp, const int32_t *ci, const T *val, int k,
-               T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *dot_out,
-               cudaStream_t st) {
+struct Plan {
+  int vec, G, nv, grid;
+};
+
+template <typename T>
+Plan plan_for(int64_t n, int k, bool aligned) {
+  const int vec = aligned ? (int)(16 / sizeof(T)) : 1;
+  const int chunks = (k + vec - 1) / vec;
+  int G = 1;
+  while ((chunks + G - 1) / G > 8 && G < 32) G <<= 1;
+  int nv = (chunks + G - 1) / G;
+  if (nv > 8) nv = 8;           // k > 32 * 8 * vec: the caller splits the columns
+  const int64_t threads = n * G;
+  int64_t grid = (threads + kSpmmThreads - 1) / kSpmmThreads;
+  const int64_t cap = (int64_t)device_sm_count() * 8;   // full occupancy, grid-stride beyond
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  return {vec, G, nv, (int)grid};
+}
+
+template <typename T, int VEC, int NV>
+void launch_v(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, const T *val,
+              int k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *part,
+              double *dot_out, unsigned *ticket, cudaStream_t st) {
   if (dot_out)
-    spmm_kernel<T, G, C, true><<<grid, kSpmmThreads, k * sizeof(double), st>>>(
-        n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out);
+    spmm_kernel<T, VEC, NV, true><<<pl.grid, kSpmmThreads, (k + kSpmmThreads) * sizeof(double), st>>>(
+        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket);
   else
-    spmm_kernel<T, G, C, false><<<grid, kSpmmThreads, 0, st>>>(n, rp, ci, val, k, alpha, X, ldx,
-                                                                beta, Y, ldy, nullptr);
+    spmm_kernel<T, VEC, NV, false><<<pl.grid, kSpmmThreads, 0, st>>>(
+        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, nullptr, nullptr, nullptr);
 }
 
-template <typename T, int G>
-void launch_g(int C, int grid, int64_t n, const int32_t *rp, const int32_t *ci, const T *val,
-              int k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy,
-              double *dot_out, cudaStream_t st) {
-  switch (C) {
-    case 1: launch_gc<T, G, 1>(grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 2: launch_gc<T, G, 2>(grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 3: launch_gc<T, G, 3>(grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    default: launch_gc<T, G, 4>(grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-  }
+template <typename T, int VEC>
+void launch_nv(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, const T *val,
+               int k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *part,
+               double *dot_out, unsigned *ticket, cudaStream_t st) {
+  if (pl.nv <= 2)
+    launch_v<T, VEC, 2>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
+  else if (pl.nv <= 4)
+    launch_v<T, VEC, 4>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
+  else if (pl.nv <= 6)
+    launch_v<T, VEC, 6>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
+  else
+    launch_v<T, VEC, 8>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
 }
 
-int spmm_grid(int64_t n, int G) {
-  const int64_t groups_per_block = kSpmmThreads / G;
-  int64_t need = (n + groups_per_block - 1) / groups_per_block;
-  const int64_t cap = (int64_t)device_sm_count() * 8;
-  if (need > cap) need = cap;
-  if (need < 1) need = 1;
-  return (int)need;
+template <typename T>
+bool aligned16(const T *X, int64_t ldx, const T *Y, int64_t ldy) {
+  constexpr int vec = 16 / sizeof(T);
+  return ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0) && (ldx % vec == 0) &&
+         (ldy % vec == 0);
 }
 
 }  // namespace
 
-int spmm_dot_blocks(int64_t n, int k) { return spmm_grid(n, spmm_shape(k).G); }
+int spmm_dot_blocks(int64_t n, int k) {
+  // the dot variant is launched by the CG step on 16-byte aligned blocks of either type;
+  // return the larger of the two plans so a partial buffer sized by it always fits
+  const Plan a = plan_for<float>(n, k, true), b = plan_for<double>(n, k, true);
+  const Plan c = plan_for<float>(n, k, false), d = plan_for<double>(n, k, false);
+  int g = a.grid;
+  if (b.grid > g) g = b.grid;
+  if (c.grid > g) g = c.grid;
+  if (d.grid > g) g = d.grid;
+  return g;
+}
 
 template <typename T>
 int launch_spmm(int64_t n, const int32_t *rp, const int32_t *ci, const T *val, int k, T alpha,
                 const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *dot_out,
-                int dot_blocks, cudaStream_t st) {
+                int dot_blocks, cudaStream_t st, double *part, unsigned *ticket) {
   if (n <= 0 || k <= 0) return GCGE_OK;
-  const SpmmShape s = spmm_shape(k);
-  if (dot_out && k > s.G * s.C) return GCGE_EINVAL;   // dot epilogue needs one column pass
-  const int grid = spmm_grid(n, s.G);
-  if (dot_out && grid != dot_blocks) return GCGE_EINVAL;
-  switch (s.G) {
-    case 1: launch_g<T, 1>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 2: launch_g<T, 2>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 4: launch_g<T, 4>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 8: launch_g<T, 8>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    case 16: launch_g<T, 16>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
-    default: launch_g<T, 32>(s.C, grid, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, dot_out, st); break;
+  constexpr int vmax = 16 / sizeof(T);
+  const bool al = aligned16<T>(X, ldx, Y, ldy);
+  const int maxk = 32 * 8 * (al ? vmax : 1);
+  if (k > maxk) {   // very wide blocks: split the columns (no fused dot across splits)
+    if (dot_out) return GCGE_EINVAL;
+    for (int j0 = 0; j0 < k; j0 += maxk) {
+      const int kk = (k - j0) < maxk ? (k - j0) : maxk;
+      GCGE_CHECK(launch_spmm<T>(n, rp, ci, val, kk, alpha, X + j0, ldx, beta, Y + j0, ldy, nullptr,
+                                0, st, nullptr, nullptr));
+    }
+    return GCGE_OK;
   }
+  const Plan pl = plan_for<T>(n, k, al);
+  if (dot_out && (pl.grid > dot_blocks || !part || !ticket)) return GCGE_EINVAL;
+  if (al)
+    launch_nv<T, vmax>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
+  else
+    launch_nv<T, 1>(pl, n, rp, ci, val, k, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, st);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
 
 template int launch_spmm<double>(int64_t, const int32_t *, const int32_t *, const double *, int,
                                  double, const double *, int64_t, double, double *, int64_t,
-                                 double *, int, cudaStream_t);
+                                 double *, int, cudaStream_t, double *, unsigned *);
 template int launch_spmm<float>(int64_t, const int32_t *, const int32_t *, const float *, int,
                                 float, const float *, int64_t, float, float *, int64_t, double *,
-                                int, cudaStream_t);
+                                int, cudaStream_t, double *, unsigned *);
 
 }  // namespace gcge

@@ -68,17 +68,26 @@ __device__ __forceinline__ void round_pair(int D, int r, int k, int &p, int &q) 
   q = a < b ? b : a;
 }
 
+// One grid barrier per round: every CTA derives the round's d/2 rotations itself
+// (into shared memory) from the diagonal and pair entries, then the grid updates the
+// 2x2 blocks of A and the rows of V.  Entries written by other CTAs are read with
+// L1-bypassing loads (__ldcg) after the barrier.
+constexpr int kMaxPairs = 512;   // d <= 1024
+
 __global__ void __launch_bounds__(kSyevThreads)
 jacobi_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restrict__ V,
-              int64_t ldv, double *__restrict__ rot, unsigned *__restrict__ sync,
+              int64_t ldv, double *__restrict__ rot_unused, unsigned *__restrict__ sync,
               int *__restrict__ flags, int max_sweeps) {
+  (void)rot_unused;
+  __shared__ double rot[kMaxPairs][3];
+  __shared__ int local_cnt;
   const int P = D / 2;
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
   const unsigned nb = gridDim.x;
   for (int64_t u = gt; u < (int64_t)d * d; u += gs) {
     const int i = (int)(u % d), j = (int)(u / d);
-    V[i + (int64_t)j * ldv] = (i == j) ? 1.0 : 0.0;
+    __stcg(V + i + (int64_t)j * ldv, (i == j) ? 1.0 : 0.0);
   }
   if (gt == 0) {
     sync[2] = 0;
@@ -90,77 +99,79 @@ jacobi_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restr
   for (; sweep < max_sweeps; ++sweep) {
     unsigned *cnt = sync + 2 + (sweep % 3);
     if (gt == 0) sync[2 + ((sweep + 1) % 3)] = 0;
+    if (threadIdx.x == 0) local_cnt = 0;
+    __syncthreads();
     for (int r = 0; r < D - 1; ++r) {
-      // phase A: rotation of every pair of this round
-      for (int64_t k = gt; k < P; k += gs) {
+      // rotations of this round (identical in every CTA)
+      for (int k = threadIdx.x; k < P; k += blockDim.x) {
         int p, q;
-        round_pair(D, r, (int)k, p, q);
+        round_pair(D, r, k, p, q);
         double c = 1.0, s = 0.0, t = 0.0;
         if (q < d) {
-          const double app = A[p + (int64_t)p * lda], aqq = A[q + (int64_t)q * lda];
-          const double apq = A[p + (int64_t)q * lda];
+          const double app = __ldcg(A + p + (int64_t)p * lda), aqq = __ldcg(A + q + (int64_t)q * lda);
+          const double apq = __ldcg(A + p + (int64_t)q * lda);
           if (apq != apq || app != app || aqq != aqq) flags[1] = 1;
           const double thr = 1e-15 * sqrt(fabs(app) * fabs(aqq));
           if (fabs(apq) > thr && fabs(apq) > 1e-300) {
             const double th = (aqq - app) / (2.0 * apq);
             t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-            c = 1.0 / sqrt(1.0 + t * t);
+            c = rsqrt(1.0 + t * t);
             s = t * c;
-            atomicAdd(cnt, 1u);
+            if (blockIdx.x == 0) atomicAdd(&local_cnt, 1);
           }
         }
-        rot[3 * k] = c;
-        rot[3 * k + 1] = s;
-        rot[3 * k + 2] = t;
+        rot[k][0] = c;
+        rot[k][1] = s;
+        rot[k][2] = t;
       }
-      if (!grid_barrier(sync, flags, nb)) return;
-      // phase B: 2x2 blocks of A, then rows of V
+      __syncthreads();
       const int64_t nblk = (int64_t)P * P;
       for (int64_t u = gt; u < nblk + (int64_t)d * P; u += gs) {
         if (u < nblk) {
           const int kr = (int)(u % P), kc = (int)(u / P);
-          const double s1 = rot[3 * kr + 1], s2 = rot[3 * kc + 1];
+          const double s1 = rot[kr][1], s2 = rot[kc][1];
           if (s1 == 0.0 && s2 == 0.0) continue;
           int pr, qr, pc, qc;
           round_pair(D, r, kr, pr, qr);
           round_pair(D, r, kc, pc, qc);
           if (kr == kc) {   // diagonal block of an active rotation: exact update
-            const double t = rot[3 * kr + 2];
-            const double apq = A[pr + (int64_t)qr * lda];
-            A[pr + (int64_t)pr * lda] -= t * apq;
-            A[qr + (int64_t)qr * lda] += t * apq;
-            A[pr + (int64_t)qr * lda] = 0.0;
-            A[qr + (int64_t)pr * lda] = 0.0;
+            const double t = rot[kr][2];
+            const double apq = __ldcg(A + pr + (int64_t)qr * lda);
+            __stcg(A + pr + (int64_t)pr * lda, __ldcg(A + pr + (int64_t)pr * lda) - t * apq);
+            __stcg(A + qr + (int64_t)qr * lda, __ldcg(A + qr + (int64_t)qr * lda) + t * apq);
+            __stcg(A + pr + (int64_t)qr * lda, 0.0);
+            __stcg(A + qr + (int64_t)pr * lda, 0.0);
             continue;
           }
-          const double c1 = rot[3 * kr], c2 = rot[3 * kc];
+          const double c1 = rot[kr][0], c2 = rot[kc][0];
           const bool vqr = qr < d, vqc = qc < d;
           double *ap = A + pr + (int64_t)pc * lda;
-          const double a = *ap;
-          const double b = vqc ? A[pr + (int64_t)qc * lda] : 0.0;
-          const double e = vqr ? A[qr + (int64_t)pc * lda] : 0.0;
-          const double f = (vqr && vqc) ? A[qr + (int64_t)qc * lda] : 0.0;
+          const double a = __ldcg(ap);
+          const double b = vqc ? __ldcg(A + pr + (int64_t)qc * lda) : 0.0;
+          const double e = vqr ? __ldcg(A + qr + (int64_t)pc * lda) : 0.0;
+          const double f = (vqr && vqc) ? __ldcg(A + qr + (int64_t)qc * lda) : 0.0;
           const double a1 = c1 * a - s1 * e, b1 = c1 * b - s1 * f;
           const double e1 = s1 * a + c1 * e, f1 = s1 * b + c1 * f;
-          *ap = c2 * a1 - s2 * b1;
-          if (vqc) A[pr + (int64_t)qc * lda] = s2 * a1 + c2 * b1;
-          if (vqr) A[qr + (int64_t)pc * lda] = c2 * e1 - s2 * f1;
-          if (vqr && vqc) A[qr + (int64_t)qc * lda] = s2 * e1 + c2 * f1;
+          __stcg(ap, c2 * a1 - s2 * b1);
+          if (vqc) __stcg(A + pr + (int64_t)qc * lda, s2 * a1 + c2 * b1);
+          if (vqr) __stcg(A + qr + (int64_t)pc * lda, c2 * e1 - s2 * f1);
+          if (vqr && vqc) __stcg(A + qr + (int64_t)qc * lda, s2 * e1 + c2 * f1);
         } else {
           const int64_t v = u - nblk;
           const int k = (int)(v % P), i = (int)(v / P);
-          const double s = rot[3 * k + 1];
+          const double s = rot[k][1];
           if (s == 0.0) continue;
-          const double c = rot[3 * k];
+          const double c = rot[k][0];
           int p, q;
           round_pair(D, r, k, p, q);
           double *vp = V + i + (int64_t)p * ldv;
           double *vq = V + i + (int64_t)q * ldv;
-          const double x = *vp, y = *vq;
-          *vp = c * x - s * y;
-          *vq = s * x + c * y;
+          const double x = __ldcg(vp), y = __ldcg(vq);
+          __stcg(vp, c * x - s * y);
+          __stcg(vq, s * x + c * y);
         }
       }
+      if (r == D - 2 && blockIdx.x == 0 && threadIdx.x == 0 && local_cnt) atomicAdd(cnt, 1u);
       if (!grid_barrier(sync, flags, nb)) return;
     }
     const unsigned done = *((volatile unsigned *)cnt);
@@ -170,6 +181,109 @@ jacobi_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restr
     }
   }
   if (gt == 0) flags[2] = sweep;
+}
+
+// Small matrices (d <= kSmallD): the whole Jacobi in one CTA with A and V in shared
+// memory and __syncthreads() between the two phases of a round.
+constexpr int kSmallD = 32;
+
+__global__ void __launch_bounds__(256)
+jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restrict__ Vout,
+                    int64_t ldv, int *__restrict__ flags, int max_sweeps) {
+  __shared__ double sA[kSmallD][kSmallD + 1];
+  __shared__ double sV[kSmallD][kSmallD + 1];
+  __shared__ double rot[kSmallD / 2][3];
+  __shared__ int cnt;
+  const int P = D / 2;
+  for (int u = threadIdx.x; u < d * d; u += blockDim.x) {
+    const int i = u % d, j = u / d;
+    sA[i][j] = A[i + (int64_t)j * lda];
+    sV[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int r = 0; r < D - 1; ++r) {
+      for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        int p, q;
+        round_pair(D, r, k, p, q);
+        double c = 1.0, s = 0.0, t = 0.0;
+        if (q < d) {
+          const double app = sA[p][p], aqq = sA[q][q], apq = sA[p][q];
+          if (apq != apq || app != app || aqq != aqq) flags[1] = 1;
+          const double thr = 1e-15 * sqrt(fabs(app) * fabs(aqq));
+          if (fabs(apq) > thr && fabs(apq) > 1e-300) {
+            const double th = (aqq - app) / (2.0 * apq);
+            t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+            atomicAdd(&cnt, 1);
+          }
+        }
+        rot[k][0] = c;
+        rot[k][1] = s;
+        rot[k][2] = t;
+      }
+      __syncthreads();
+      const int nblk = P * P;
+      for (int u = threadIdx.x; u < nblk + d * P; u += blockDim.x) {
+        if (u < nblk) {
+          const int kr = u % P, kc = u / P;
+          const double s1 = rot[kr][1], s2 = rot[kc][1];
+          if (s1 == 0.0 && s2 == 0.0) continue;
+          int pr, qr, pc, qc;
+          round_pair(D, r, kr, pr, qr);
+          round_pair(D, r, kc, pc, qc);
+          if (kr == kc) {
+            const double t = rot[kr][2];
+            const double apq = sA[pr][qr];
+            sA[pr][pr] -= t * apq;
+            sA[qr][qr] += t * apq;
+            sA[pr][qr] = 0.0;
+            sA[qr][pr] = 0.0;
+            continue;
+          }
+          const double c1 = rot[kr][0], c2 = rot[kc][0];
+          const bool vqr = qr < d, vqc = qc < d;
+          const double a = sA[pr][pc];
+          const double b = vqc ? sA[pr][qc] : 0.0;
+          const double e = vqr ? sA[qr][pc] : 0.0;
+          const double f = (vqr && vqc) ? sA[qr][qc] : 0.0;
+          const double a1 = c1 * a - s1 * e, b1 = c1 * b - s1 * f;
+          const double e1 = s1 * a + c1 * e, f1 = s1 * b + c1 * f;
+          sA[pr][pc] = c2 * a1 - s2 * b1;
+          if (vqc) sA[pr][qc] = s2 * a1 + c2 * b1;
+          if (vqr) sA[qr][pc] = c2 * e1 - s2 * f1;
+          if (vqr && vqc) sA[qr][qc] = s2 * e1 + c2 * f1;
+        } else {
+          const int v = u - nblk;
+          const int k = v % P, i = v / P;
+          const double s = rot[k][1];
+          if (s == 0.0) continue;
+          const double c = rot[k][0];
+          int p, q;
+          round_pair(D, r, k, p, q);
+          const double x = sV[i][p], y = sV[i][q];
+          sV[i][p] = c * x - s * y;
+          sV[i][q] = s * x + c * y;
+        }
+      }
+      __syncthreads();
+    }
+    if (cnt == 0) {
+      ++sweep;
+      break;
+    }
+    __syncthreads();
+  }
+  for (int u = threadIdx.x; u < d * d; u += blockDim.x) {
+    const int i = u % d, j = u / d;
+    A[i + (int64_t)j * lda] = sA[i][j];
+    Vout[i + (int64_t)j * ldv] = sV[i][j];
+  }
+  if (threadIdx.x == 0) flags[2] = sweep;
 }
 
 // Ascending order by rank; ties keep the original index order.
@@ -208,6 +322,7 @@ int SyevWork::alloc(int d) {
 }
 
 void SyevWork::free_all() {
+  mp.free_all();
   cudaFree(rot);
   cudaFree(V);
   cudaFree(sync);
@@ -225,20 +340,36 @@ int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevW
   GCGE_CHECK(work.alloc(d));
   const int D = d + (d & 1);
   const int P = D / 2;
+  if (d > 2 * kMaxPairs) return GCGE_EINVAL;
   const int64_t items = (int64_t)P * P + (int64_t)d * P;
   int grid = (int)((items + kSyevThreads - 1) / kSyevThreads);
+  if (grid > device_sm_count()) grid = device_sm_count();
   if (d <= 48) grid = 1;                    // small leaves: one CTA, barrier = local
   if (grid > work.coop_grid) grid = work.coop_grid;
   if (grid < 1) grid = 1;
   GCGE_CUDA(cudaMemsetAsync(work.sync, 0, sizeof(unsigned) * 8, st));
   GCGE_CUDA(cudaMemsetAsync(work.flags, 0, sizeof(int) * 4, st));
+  if (work.mixed && d > kSmallD) {
+    const int s = syev_mixed(d, A, lda, w, Q, ldq, work.mp, work.flags, sweeps, st);
+    if (s == GCGE_OK) {
+      GCGE_CUDA(cudaStreamSynchronize(st));
+      return GCGE_OK;
+    }
+    if (s != GCGE_EINVAL) return s;
+    GCGE_CUDA(cudaMemsetAsync(work.flags, 0, sizeof(int) * 4, st));   // fall back to FP64 Jacobi
+  }
   int max_sweeps = 60;
   double *Vw = work.V;
   int64_t ldv = d;
-  void *args[] = {&d, (void *)&D, &A, &lda, &Vw, &ldv, &work.rot, &work.sync, &work.flags,
-                  &max_sweeps};
-  GCGE_CUDA(cudaLaunchCooperativeKernel((void *)jacobi_kernel, dim3(grid), dim3(kSyevThreads),
-                                        args, 0, st));
+  if (d <= kSmallD) {
+    jacobi_small_kernel<<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);
+    GCGE_LAUNCH_CHECK();
+  } else {
+    void *args[] = {&d, (void *)&D, &A, &lda, &Vw, &ldv, &work.rot, &work.sync, &work.flags,
+                    &max_sweeps};
+    GCGE_CUDA(cudaLaunchCooperativeKernel((void *)jacobi_kernel, dim3(grid), dim3(kSyevThreads),
+                                          args, 0, st));
+  }
   sort_eig_kernel<<<ceil_div(d, 128), 128, 0, st>>>(d, A, lda, Vw, ldv, w, Q, ldq, work.flags);
   GCGE_LAUNCH_CHECK();
   GCGE_CUDA(cudaMemcpyAsync(work.h_flags, work.flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));

@@ -4,6 +4,19 @@
 
 namespace gcge {
 
+// Work area of the mixed-precision eigensolver (FP32 cluster Jacobi + FP64 polish).
+struct MpWork {
+  float *V32 = nullptr, *gn = nullptr;
+  double *V = nullptr, *T1 = nullptr, *T2 = nullptr, *Bm = nullptr, *lam = nullptr;
+  double *dinfo = nullptr;
+  int *ints = nullptr;
+  double *h = nullptr;
+  int *hi = nullptr;
+  int dcap = 0;
+  int alloc(int d);
+  void free_all();
+};
+
 struct SyevWork {
   double *rot = nullptr;      // 3 * D/2 rotation parameters of one round
   double *V = nullptr;        // d x d accumulated rotations (column-major, ld = dcap)
@@ -12,9 +25,17 @@ struct SyevWork {
   int *h_flags = nullptr;     // pinned mirror of flags
   int dcap = 0;
   int coop_grid = 0;          // co-resident CTAs for the cooperative launch
+  MpWork mp;                  // mixed-precision path
+  int mixed = 1;              // 1: try the mixed-precision path for d > 32
   int alloc(int d);
   void free_all();
 };
+
+// Mixed-precision eigensolve of the symmetric A (not modified); GCGE_EINVAL when it
+// does not apply (size, a cluster of near-equal eigenvalues wider than 32, or no
+// convergence), in which case the caller uses the FP64 Jacobi.
+int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_t ldq,
+               MpWork &mw, int *flags_dev, int *sweeps, cudaStream_t st);
 
 // A (d x d col-major, lda) is destroyed; w[d] ascending; Q (ldq) eigenvectors.
 // Synchronises the stream.  Returns GCGE_OK / GCGE_ETIMEOUT / GCGE_ENAN / GCGE_ECUDA.
