@@ -351,3 +351,103 @@ class Solver:
 def build():
     from .build import build as _b
     return _b()
+
+
+# ------------------------------------------------------------------ autograd
+def _torch():
+    import torch
+    return torch
+
+
+class _CsrDev:
+    """A CSR matrix held as device tensors (row_ptr, col_idx, values)."""
+
+    def __init__(self, M, device="cuda"):
+        torch = _torch()
+        self.n_rows = M.shape[0]
+        self.rp = torch.tensor(np.asarray(M.indptr, dtype=np.int32), device=device)
+        self.ci = torch.tensor(np.asarray(M.indices, dtype=np.int32), device=device)
+        self.val = torch.tensor(np.asarray(M.data, dtype=np.float64), device=device)
+
+
+class CellMap:
+    """Linear map c -> A(c).data given by a sparse Jacobian J (nnz x cells), applied and
+    transposed with the library's SpMM (k = 1)."""
+
+    def __init__(self, J):
+        self.J = _CsrDev(J)
+        self.JT = _CsrDev(J.T.tocsr())
+        self.nnz = J.shape[0]
+        self.ncell = J.shape[1]
+
+    def apply(self, c):
+        torch = _torch()
+        out = torch.empty(self.nnz, dtype=torch.float64, device=c.device)
+        gcge_spmm_f64(self.nnz, self.J.rp, self.J.ci, self.J.val, 1, 1.0, c.contiguous(), 1, 0.0,
+                      out, 1)
+        return out
+
+    def apply_t(self, g):
+        torch = _torch()
+        out = torch.empty(self.ncell, dtype=torch.float64, device=g.device)
+        gcge_spmm_f64(self.ncell, self.JT.rp, self.JT.ci, self.JT.val, 1, 1.0, g.contiguous(), 1,
+                      0.0, out, 1)
+        return out
+
+
+def cells_to_values(c, cmap: CellMap):
+    """Differentiable A(c).data = J c (backward: J^T g on the library's SpMM)."""
+    torch = _torch()
+
+    class _F(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, cc):
+            return cmap.apply(cc)
+
+        @staticmethod
+        def backward(ctx, g):
+            return cmap.apply_t(g)
+
+    return _F.apply(c)
+
+
+class EigGCG:
+    """Differentiable smallest-nev eigenpairs of A(a_vals) x = lambda B x.
+
+    ``EigGCG.apply(a_vals, pattern, B, nev, bs, tol, adj_tol, opts)`` returns
+    (eigenvalues (nev,), eigenvectors (n, nev)) as device tensors; the backward pass
+    calls gcge_eig_grad (adjoint kernel) and returns dL/da_vals on A's CSR pattern.
+    pattern = (row_ptr, col_idx) device int32 tensors; B a scipy CSR or None.
+    """
+
+    @staticmethod
+    def apply(a_vals, pattern, B, nev, bs, tol=1e-8, adj_tol=1e-12, opts=None):
+        torch = _torch()
+        rp, ci = pattern
+        opts = dict(opts or {})
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, av):
+                solver = Solver((rp, ci, av.detach().contiguous()), B, nev, bs, tol, **opts)
+                n = solver.n
+                ev_buf = torch.empty((nev, n), dtype=torch.float64, device=av.device)
+                ev, _ = solver.solve(evecs_device=ev_buf)
+                ctx.solver = solver
+                ctx.n = n
+                return (torch.tensor(ev, dtype=torch.float64, device=av.device),
+                        ev_buf.t())
+
+            @staticmethod
+            def backward(ctx, g_ev, g_x):
+                solver = ctx.solver
+                w = (g_ev.detach().cpu().numpy().astype(np.float64) if g_ev is not None
+                     else np.zeros(nev))
+                gx = None
+                if g_x is not None:
+                    gx = g_x.detach().to(torch.float64).contiguous()
+                out = torch.empty(ci.numel(), dtype=torch.float64, device=rp.device)
+                gcge_eig_grad(solver.h, nev, w, gx, nev, out, adj_tol)
+                return out
+
+        return _F.apply(a_vals)

@@ -688,6 +688,8 @@ template int add_cols<float, double>(int64_t, int, const float *, int64_t, doubl
                                      cudaStream_t);
 template int add_cols<float, float>(int64_t, int, const float *, int64_t, float *, int64_t,
                                     cudaStream_t);
+template int add_cols<double, double>(int64_t, int, const double *, int64_t, double *, int64_t,
+                                      cudaStream_t);
 
 template int copy_cols<double, double>(int64_t, int, const double *, int64_t, double *, int64_t,
                                        const double *, cudaStream_t);

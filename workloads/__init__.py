@@ -40,7 +40,8 @@ import scipy.sparse as sp
 __all__ = [
     "Pencil", "fd2d", "q1_kron", "q1_var", "fd3d_var", "random_sparse_spd",
     "lognormal_cells", "initial_block", "splitmix64", "CONFIGS", "make_config",
-    "fd2d_eigs", "q1_eigs", "fd3d_eigs_const",
+    "fd2d_eigs", "q1_eigs", "fd3d_eigs_const", "q1_cell_nodes", "q1_cell_jacobian",
+    "q1grad_setup",
 ]
 
 
@@ -212,6 +213,55 @@ def _stencil_to_csr(N, offs, valsA, valsB):
     return out
 
 
+def q1_cell_nodes(N: int) -> np.ndarray:
+    """(N+1)^3 x 8 interior-node indices of every Q1 cell (-1 for Dirichlet nodes).
+
+    Local node a = a0*4 + a1*2 + a2 of cell e = (e0, e1, e2) is node (e0+a0-1, ...).
+    """
+    e = np.arange(N + 1)
+    E0, E1, E2 = np.meshgrid(e, e, e, indexing="ij")
+    out = np.empty(((N + 1) ** 3, 8), dtype=np.int64)
+    for a0 in (0, 1):
+        for a1 in (0, 1):
+            for a2 in (0, 1):
+                i0, i1, i2 = E0 + a0 - 1, E1 + a1 - 1, E2 + a2 - 1
+                ok = (i0 >= 0) & (i0 < N) & (i1 >= 0) & (i1 < N) & (i2 >= 0) & (i2 < N)
+                out[:, a0 * 4 + a1 * 2 + a2] = np.where(ok, (i0 * N + i1) * N + i2, -1).ravel()
+    return out
+
+
+def q1_cell_jacobian(N: int, A: sp.csr_matrix) -> sp.csr_matrix:
+    """J (nnz x (N+1)^3) with A(c).data = J @ c for the Q1 pencil of ``q1_var``.
+
+    Row t of J belongs to the t-th stored nonzero (p, q) of A's CSR pattern; entry
+    (t, e) is the cell stiffness Khat_e[a, b] of the local pair that maps to (p, q).
+    """
+    h = 1.0 / (N + 1)
+    k1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    m1 = np.array([[2.0, 1.0], [1.0, 2.0]]) / 6.0
+    Khat = h * (np.kron(k1, np.kron(m1, m1)) + np.kron(m1, np.kron(k1, m1))
+                + np.kron(m1, np.kron(m1, k1)))
+    nodes = q1_cell_nodes(N)
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(A.indptr))
+    keys = rows * n + A.indices.astype(np.int64)
+    ri, ci, vi = [], [], []
+    cells = np.arange(nodes.shape[0])
+    for a in range(8):
+        for b in range(8):
+            p, q = nodes[:, a], nodes[:, b]
+            ok = (p >= 0) & (q >= 0)
+            pos = np.searchsorted(keys, p[ok] * n + q[ok])
+            ri.append(pos)
+            ci.append(cells[ok])
+            vi.append(np.full(pos.size, Khat[a, b]))
+    J = sp.csr_matrix((np.concatenate(vi), (np.concatenate(ri), np.concatenate(ci))),
+                      shape=(A.nnz, nodes.shape[0]))
+    J.sum_duplicates()
+    J.sort_indices()
+    return J
+
+
 # ----------------------------------------------------------------------------
 # 3D 7-point finite-volume diffusion with variable coefficient
 # ----------------------------------------------------------------------------
@@ -340,6 +390,22 @@ CONFIGS = {
     "q1grad_48": dict(nev=10, bs=2),
     "q1_160": dict(nev=1000, bs=100),
 }
+
+
+def q1grad_setup(N: int, seed: int, nev: int = 10, sub: int = 8, n_fd: int = 64) -> dict:
+    """Loss ingredients of the differentiation workload (Q1 on N^3, lognormal c):
+    c (cells), the 0/1 node indicator of a seeded sub^3 node block S, weights w ~ U(0,1)
+    for the eigenvector terms, and n_fd seeded cells for finite-difference checks.
+    L = sum_i lambda_i + sum_i w_i x_i^T B_S x_i with B_S = D_S B D_S."""
+    rng = np.random.default_rng(seed + 1000)
+    c = lognormal_cells((N + 1,) * 3, 0.5, seed)
+    sub = min(sub, N)
+    o = rng.integers(0, N - sub + 1, size=3)
+    mask = np.zeros((N, N, N))
+    mask[o[0]:o[0] + sub, o[1]:o[1] + sub, o[2]:o[2] + sub] = 1.0
+    w = rng.uniform(0.0, 1.0, nev)
+    fd = rng.choice((N + 1) ** 3, size=min(n_fd, (N + 1) ** 3), replace=False)
+    return {"c": c, "S": mask.ravel(), "w": w, "fd_cells": fd}
 
 
 def make_config(name: str, seed: int = 0, N: int | None = None) -> Pencil:
