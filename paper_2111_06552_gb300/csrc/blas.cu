@@ -474,6 +474,14 @@ template <typename T>
 int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T *Y,
             int64_t ldy, double beta, double *C, int64_t ldc, Scratch &ws, cudaStream_t st);
 
+int gram_reduce_launch(int m, int k, int splits, const double *part, double alpha, double beta,
+                       double *C, int64_t ldc, cudaStream_t st) {
+  gram_reduce_kernel<<<elem_grid((int64_t)m * k), 256, 0, st>>>(m, k, splits, part, alpha, beta, C,
+                                                                 ldc);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+
 template <typename T>
 int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
          double beta, double *C, int64_t ldc, int tc, Scratch &ws, cudaStream_t st) {

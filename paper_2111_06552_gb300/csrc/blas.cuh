@@ -32,6 +32,9 @@ template <typename T>
 int vc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
        int64_t ldc, double beta, T *Y, int64_t ldy, int tc, cudaStream_t st);
 
+// Error flag of the tensor-core kernels (1 once a bounded mbarrier wait ran out).
+int tc_error_flag(int *host_val, cudaStream_t st);
+
 // Small dense FP64 column-major GEMM: C = alpha op(A) op(B) + beta C.
 int dgemm_small(char ta, char tb, int m, int n, int k, double alpha, const double *A, int64_t lda,
                 const double *B, int64_t ldb, double beta, double *C, int64_t ldc,

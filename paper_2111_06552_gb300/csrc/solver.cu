@@ -1146,6 +1146,9 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     GCGE_CHECK(e1.setup(sx, h->nev, h->store_cap));
     const int s1 = e1.run(X0d, ld0, nullptr, 0);
     if (s1 != GCGE_OK && s1 != GCGE_ENOTCONV) return s1;
+    int tc_err = 0;   // a tensor-core kernel whose bounded wait ran out leaves a flag
+    GCGE_CHECK(tc_error_flag(&tc_err, h->st));
+    if (tc_err) return GCGE_ETIMEOUT;
     it1 = e1.iterations();
     add_stats(h, e1);
     GCGE_CUDA(cudaMalloc(&X1, sizeof(float) * (size_t)h->n * sx));
