@@ -138,8 +138,12 @@ int gcge_vc_f32(int64_t n, int d, int q, double alpha, const float *V, int64_t l
   if (n < 0 || d < 0 || q < 0 || ldv < d || ldc < d || ldy < q) return GCGE_EINVAL;
   if (q == 0 || n == 0) return GCGE_OK;
   if (bad_ptr(Y) || (d > 0 && (bad_ptr(V) || bad_ptr(C)))) return GCGE_EINVAL;
-  g_launches += 1;
-  return vc<float>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, tc, as_stream(stream));
+  g_launches += tc ? 2 : 1;
+  Scratch ws;
+  cudaStream_t st = as_stream(stream);
+  int s = vc<float>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, tc, st, &ws);
+  ws.release(st);
+  return s;
 }
 
 int gcge_syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, int *sweeps,

@@ -555,14 +555,14 @@ int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, i
 
 template <typename T>
 int vc_tc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
-          int64_t ldc, double beta, T *Y, int64_t ldy, cudaStream_t st);
+          int64_t ldc, double beta, T *Y, int64_t ldy, cudaStream_t st, Scratch *ws);
 
 template <typename T>
 int vc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
-       int64_t ldc, double beta, T *Y, int64_t ldy, int tc, cudaStream_t st) {
+       int64_t ldc, double beta, T *Y, int64_t ldy, int tc, cudaStream_t st, Scratch *ws) {
   if (n <= 0 || q <= 0) return GCGE_OK;
   if (d < 0) return GCGE_EINVAL;   // d == 0 leaves Y = beta * Y
-  if (tc) return vc_tc<T>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, st);
+  if (tc) return vc_tc<T>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, st, ws);
   dim3 grid((unsigned)ceil_div(n, VR), (unsigned)ceil_div(q, VQ));
   vc_kernel<T><<<grid, 256, 0, st>>>(n, d, q, (T)alpha, V, ldv, C, ldc, (T)beta, Y, ldy);
   GCGE_LAUNCH_CHECK();
@@ -668,7 +668,7 @@ int shifted_values(int64_t nnz_u, const int *mapA, const double *valA, const int
   template int gram<T>(int64_t, int, int, double, const T *, int64_t, const T *, int64_t, double, \
                        double *, int64_t, int, Scratch &, cudaStream_t);                         \
   template int vc<T>(int64_t, int, int, double, const T *, int64_t, const double *, int64_t,      \
-                     double, T *, int64_t, int, cudaStream_t);                                    \
+                     double, T *, int64_t, int, cudaStream_t, Scratch *);                         \
   template int col_dots<T>(int64_t, int, const T *, int64_t, const T *, int64_t, double *,       \
                            Scratch &, cudaStream_t);                                             \
   template int residual_parts<T>(int64_t, int, const T *, int64_t, const T *, int64_t,           \

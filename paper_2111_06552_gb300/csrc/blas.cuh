@@ -28,9 +28,11 @@ int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, i
                        double *ws, int64_t ws_doubles, cudaStream_t st);
 
 // Y(n x q) = alpha * V(n x d) C(d x q col-major FP64) + beta * Y.
+// `ws` (optional) holds the split operand of the tensor-core path.
 template <typename T>
 int vc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
-       int64_t ldc, double beta, T *Y, int64_t ldy, int tc, cudaStream_t st);
+       int64_t ldc, double beta, T *Y, int64_t ldy, int tc, cudaStream_t st,
+       Scratch *ws = nullptr);
 
 // Error flag of the tensor-core kernels (1 once a bounded mbarrier wait ran out).
 int tc_error_flag(int *host_val, cudaStream_t st);

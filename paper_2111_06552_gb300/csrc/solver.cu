@@ -308,9 +308,19 @@ class Engine {
   bool checks = false;
   bool stagnated = false;
   int stagnation_limit = 0;   // > 0: stop after this many iterations without a new lock
+                              // or a halving of the first unconverged residual
   KProf *prof = nullptr;      // per-kernel-class event profile (null: off)
   bool cg_fp32 = false;       // FP64 engine: run the inner CG in FP32 on the FP64 residual
   bool use_p = true;          // build P (STEP 5); the refinement phase may go without it
+  bool allow_move = true;     // moving mechanism when the handle asks for it
+  // Reservoir of start vectors (FP32, n x nres, ascending): the X window is filled from
+  // its first columns and, as pairs lock, refilled from the next ones, which enter the
+  // iteration beside W (so their rows of Abar come from the Gram product).
+  void set_reservoir(const float *Z, int64_t ldz, int nz) {
+    res_ = Z;
+    ldres_ = ldz;
+    nres_ = nz;
+  }
 
  private:
   gcge_handle *h_;
@@ -363,6 +373,11 @@ class Engine {
   // iteration state
   int off_ = 0, kx_ = 0, np_ = 0, nw_ = 0, nb_old_ = 0, lw_ = 0;
   int nlock_ = 0, it_ = 0;
+  int kgrow_ = 0;                  // extra Ritz vectors the next RR keeps (window refill)
+  double first_res_ = 0.0;         // residual of the first unconverged column (STEP 4)
+  const float *res_ = nullptr;
+  int64_t ldres_ = 0;
+  int nres_ = 0, res_next_ = 0;
   bool done_ = false;
   std::vector<double> lam_lock_, lam_h_;
   StepTimer tm_;
@@ -418,7 +433,7 @@ class Engine {
     g_launches += 1;
     ProfScope ps(prof, GCGE_K_VC, (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T),
                  2.0 * n_ * d * q);
-    return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc(), st_);
+    return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc(), st_, &ws_);
   }
   int copyT(int k, const T *X, int64_t ldx, T *Y, int64_t ldy) {
     g_launches += 1;
@@ -793,6 +808,7 @@ int Engine<T>::convergence(const T *X, int *c_out, int *chunk_start, int *chunk_
       const double r = std::sqrt(std::max(h_d_[j], 0.0)) /
                        (std::fabs(lam) * std::sqrt(std::max(h_d_[m + j], 1e-300)));
       if (!(r < tol_)) {
+        first_res_ = r;
         stop = true;
         break;
       }
@@ -921,6 +937,8 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
   GCGE_CHECK(copyT(sizeX_, TMP2_, ldW_, V_[cur_], ldV_));
   toc(1);
   kx_ = sizeX_;
+  kgrow_ = 0;
+  res_next_ = (res_ && X0f == res_) ? sizeX_ : 0;
   np_ = nw_ = 0;
   nb_old_ = 0;
   lw_ = 0;
@@ -929,7 +947,8 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
   done_ = false;
   lam_lock_.clear();
   bool first = true;
-  int since_lock = 0;
+  int since_lock = 0;            // iterations without a new lock and without progress
+  double best_res = 1e300;       // best residual of the first unconverged column
   while (true) {
     ++it_;
     const int d = kx_ + np_ + nw_;
@@ -940,13 +959,22 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     GCGE_CHECK(rayleigh_ritz(first, d));
     lam_h_.resize(d);
     GCGE_CHECK(read_d(theta_, lam_h_.data(), d));
+    if (kgrow_ > 0) {   // reservoir vectors joined last iteration: the window grows back
+      kx_ = std::min(kx_ + kgrow_, d);
+      kgrow_ = 0;
+    }
     GCGE_CHECK(vcT(d, kx_, 1.0, Va, ldV_, Qe_, dmax_, 0.0, V_[nxt], ldV_));
     toc(3);
     // ---- STEP 4: convergence, prefix locking into the store
     tic();
     int c = 0, cs = 0, cl = 0;
+    first_res_ = 0.0;
     GCGE_CHECK(convergence(V_[nxt], &c, &cs, &cl));
-    const bool move = h_->moving && (lw_ + c) >= 2 * bs_ && nlock_ + c < nev_;
+    // with a reservoir the window is refilled from it; the moving mechanism takes over
+    // once it is used up
+    const bool reservoir_left = res_ && res_next_ < nres_;
+    const bool move = allow_move && !reservoir_left && h_->moving && (lw_ + c) >= 2 * bs_ &&
+                      nlock_ + c < nev_;
     if (c > 0) {
       if (nlock_ + c > store_cap_) {
         record_message("locked-vector store overflow");
@@ -955,6 +983,10 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
       GCGE_CHECK(copyT(c, V_[nxt], ldV_, store_ + nlock_, ldS_));
       for (int j = 0; j < c; ++j) lam_lock_.push_back(lam_h_[j]);
       nlock_ += c;
+      since_lock = 0;
+      best_res = 1e300;
+    } else if (first_res_ < 0.5 * best_res) {   // still converging: not stagnant
+      best_res = first_res_;
       since_lock = 0;
     } else {
       ++since_lock;
@@ -1023,9 +1055,23 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     toc(6);
     // ---- STEP 2: W against [store, X_a, P], then Algorithm 3
     tic();
+    int rres = 0;   // reservoir vectors that refill the window, orthogonalised with W
+    if (res_ && res_next_ < nres_ && kxn < sizeX_) {
+      rres = std::min(nres_ - res_next_, sizeX_ - kxn);
+      rres = std::min(rres, (int)ldW_ - bsn);
+      rres = std::min(rres, dmax_ - (kxn + npn + bsn));
+      rres = std::max(rres, 0);
+      if (rres > 0) {
+        g_launches += 1;
+        GCGE_CHECK(copy_cols<float, T>(n_, rres, res_ + res_next_, ldres_, TMP2_ + bsn, ldW_,
+                                       nullptr, st_));
+        res_next_ += rres;
+      }
+    }
     QPart parts[2] = {{store_, ldS_, nlock_}, {V_[nxt] + xoff, ldV_, kxn + npn}};
     int nwn = 0;
-    GCGE_CHECK(borth(TMP2_, bsn, parts, 2, &nwn));
+    GCGE_CHECK(borth(TMP2_, bsn + rres, parts, 2, &nwn));
+    kgrow_ = rres;
     if (nwn > 0) GCGE_CHECK(copyT(nwn, TMP2_, ldW_, V_[nxt] + xoff + kxn + npn, ldV_));
     toc(2);
     if (prof) prof->harvest();
@@ -1136,7 +1182,9 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
   const int sx = h->size_x;
   KProf prof;
   prof.st = h->st;
-  float *X1 = nullptr;
+  float *Z = nullptr;   // phase-1 vectors, ascending: locked store, then the unlocked window
+  int nz = 0;
+  const int64_t ldz = round_up(h->store_cap, 4);
   int it1 = 0;
   {
     Engine<float> e1(h, std::max(h->opt.mixed_switch_tol, h->tol), h->opt.max_iter);
@@ -1151,32 +1199,39 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     if (tc_err) return GCGE_ETIMEOUT;
     it1 = e1.iterations();
     add_stats(h, e1);
-    GCGE_CUDA(cudaMalloc(&X1, sizeof(float) * (size_t)h->n * sx));
-    const int take_s = std::min(e1.nlock(), sx);
-    const int take_x = std::min(e1.kx(), sx - take_s);
+    const int take_s = std::min(e1.nlock(), h->store_cap);
+    const int take_x = std::min(e1.kx(), h->store_cap - take_s);
+    nz = std::max(take_s + take_x, sx);
+    GCGE_CUDA(cudaMalloc(&Z, sizeof(float) * (size_t)h->n * ldz));
     if (take_s > 0)
-      GCGE_CHECK(copy_cols<float, float>(h->n, take_s, e1.store(), e1.ld_store(), X1, sx, nullptr,
+      GCGE_CHECK(copy_cols<float, float>(h->n, take_s, e1.store(), e1.ld_store(), Z, ldz, nullptr,
                                          h->st));
     if (take_x > 0)
-      GCGE_CHECK(copy_cols<float, float>(h->n, take_x, e1.xa(), e1.ldv(), X1 + take_s, sx,
+      GCGE_CHECK(copy_cols<float, float>(h->n, take_x, e1.xa(), e1.ldv(), Z + take_s, ldz,
                                          nullptr, h->st));
-    if (take_s + take_x < sx)
-      GCGE_CHECK(random_block<float>(h->n, sx - take_s - take_x, h->opt.seed + 1,
-                                     X1 + take_s + take_x, sx, h->st));
+    if (take_s + take_x < nz)
+      GCGE_CHECK(random_block<float>(h->n, nz - take_s - take_x, h->opt.seed + 1,
+                                     Z + take_s + take_x, ldz, h->st));
     GCGE_CUDA(cudaStreamSynchronize(h->st));
   }
   *iters32 = it1;
   int s;
   {
-    // phase 2: every unconverged column is active at once (block size nev) and the
-    // inexact inner CG runs in FP32 on the FP64 residual
+    // phase 2: FP64 iteration started from the phase-1 vectors; without the moving
+    // mechanism every wanted column is active at once (block size nev), with it the
+    // window of size_x is refilled from the phase-1 vectors as pairs lock.  The inexact
+    // inner CG runs in FP32 on the FP64 residual; no P.
+    const int bs2 = h->moving ? h->bs : std::min(h->nev, sx);
     Engine<double> e2(h, h->tol, std::max(1, h->opt.max_iter - it1));
     e2.checks = h->opt.checks != 0;
     e2.cg_fp32 = true;
     e2.use_p = false;
     if (h->opt.profile) e2.prof = &prof;
-    s = e2.setup(sx, h->nev, h->store_cap, std::min(h->nev, sx));
-    if (s == GCGE_OK) s = e2.run(nullptr, 0, X1, sx);
+    s = e2.setup(sx, h->nev, h->store_cap, bs2);
+    if (s == GCGE_OK) {
+      e2.set_reservoir(Z, ldz, nz);
+      s = e2.run(nullptr, 0, Z, ldz);
+    }
     *iters = it1 + e2.iterations();
     add_stats(h, e2);
     if (s == GCGE_OK || s == GCGE_ENOTCONV) {
@@ -1184,7 +1239,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
       if (s2 != GCGE_OK) s = s2;
     }
   }
-  cudaFree(X1);
+  cudaFree(Z);
   return s;
 }
 

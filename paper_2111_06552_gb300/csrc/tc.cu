@@ -23,129 +23,16 @@
 #include <algorithm>
 
 #include "blas.cuh"
+#include "tcgen05.cuh"
 
 namespace gcge {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kTcThreads = 256;
 constexpr int kKC = 16;                        // K rows per staged chunk (2 MMA k-steps)
-constexpr long long kWaitLimit = 1ll << 26;
-
-__device__ __forceinline__ uint32_t su32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major, no swizzle (core matrices of 8 rows x 16 B);
-// lbo = byte distance between core matrices along K, sbo = along M/N.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1u << 46;   // descriptor version of tcgen05
-  return d;                  // base offset 0, layout type 0 (no swizzle)
-}
-
-// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
-      "l"(ad), "l"(bd), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase; false (and the error flag set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *err) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if (i > 64) __nanosleep(32);
-  }
-  atomicExch(err, 1);
-  return false;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   su32(dst_smem)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-
-// 8 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-  lo = x - hi;
-}
-
-// Byte offset of element (row, kk) inside a K-major operand stage of `rows` rows and
-// kKC K-columns: [kstep][rowgroup][kcore][8 rows][4 elements].
-__device__ __forceinline__ uint32_t kmaj_off(int row, int kk, int rows) {
-  const int ks = kk >> 3, kc = (kk >> 2) & 1, e = kk & 3;
-  return (uint32_t)(ks * (rows / 8) * 256 + (row >> 3) * 256 + kc * 128 + (row & 7) * 16 + e * 4);
-}
-
-__host__ __device__ inline uint32_t tmem_cols_for(int cols) {
-  uint32_t c = 32;
-  while ((int)c < cols) c <<= 1;
-  return c;
-}
 
 // ------------------------------------------------------------------------- Gram
 // Dynamic smem: 2 stages x [A_hi | A_lo | B_hi | B_lo], A = MT*128 rows, B = Np rows.
@@ -165,7 +52,7 @@ gram_tc_kernel(int64_t n, int m, int k, int MT, int Np, const float *__restrict_
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   tc_fence_before();
   __syncthreads();
@@ -182,7 +69,7 @@ gram_tc_kernel(int64_t n, int m, int k, int MT, int Np, const float *__restrict_
     const int s = c & 1;
     unsigned char *st = sm + (size_t)s * stage_bytes;
     if (c >= 2) {   // the MMAs that read this stage two chunks ago must be done
-      ok = mbar_wait(&bar[s], (uses[s] - 1) & 1, err);
+      ok = mbar_wait(&bar[s], (uses[s] - 1) & 1, err, nullptr);
       if (!ok) break;
     }
     const int64_t rb = r0 + (int64_t)c * kKC;
@@ -222,9 +109,9 @@ gram_tc_kernel(int64_t n, int m, int k, int MT, int Np, const float *__restrict_
           const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
           const uint32_t dt = tmem + t * Np;
           const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(dt, dah, dbh, idesc, acc0);
-          mma_tf32(dt, dah, dbl, idesc, 1u);
-          mma_tf32(dt, dal, dbh, idesc, 1u);
+          mma_ss(dt, dah, dbh, idesc, acc0);
+          mma_ss(dt, dah, dbl, idesc, 1u);
+          mma_ss(dt, dal, dbh, idesc, 1u);
         }
       }
       mma_commit(&bar[s]);
@@ -235,7 +122,7 @@ gram_tc_kernel(int64_t n, int m, int k, int MT, int Np, const float *__restrict_
   // wait for the last MMAs (both stages), bounded
   for (int s = 0; s < 2; ++s)
     if (uses[s] > 0) {
-      if (!mbar_wait(&bar[s], (uses[s] - 1) & 1, err)) ok = false;
+      if (!mbar_wait(&bar[s], (uses[s] - 1) & 1, err, nullptr)) ok = false;
     }
   tc_fence_after();
   if (ok && nchunks > 0 && warp < 4) {
@@ -283,7 +170,7 @@ vc_tc_kernel(int64_t n, int d, int q, int Np, float alpha, const float *__restri
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   tc_fence_before();
   __syncthreads();
@@ -297,7 +184,7 @@ vc_tc_kernel(int64_t n, int d, int q, int Np, float alpha, const float *__restri
     const int s = c & 1;
     unsigned char *st = sm + (size_t)s * stage_bytes;
     if (c >= 2) {
-      ok = mbar_wait(&bar[s], (uses[s] - 1) & 1, err);
+      ok = mbar_wait(&bar[s], (uses[s] - 1) & 1, err, nullptr);
       if (!ok) break;
     }
     const int k0 = c * kKC;
@@ -331,9 +218,9 @@ vc_tc_kernel(int64_t n, int d, int q, int Np, float alpha, const float *__restri
         const uint64_t dah = smem_desc(ah, 128, 256), dal = smem_desc(al, 128, 256);
         const uint64_t dbh = smem_desc(bh, 128, 256), dbl = smem_desc(bl, 128, 256);
         const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, dah, dbh, idesc, acc0);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+        mma_ss(tmem, dah, dbh, idesc, acc0);
+        mma_ss(tmem, dah, dbl, idesc, 1u);
+        mma_ss(tmem, dal, dbh, idesc, 1u);
       }
       mma_commit(&bar[s]);
     }
@@ -342,7 +229,7 @@ vc_tc_kernel(int64_t n, int d, int q, int Np, float alpha, const float *__restri
   }
   for (int s = 0; s < 2; ++s)
     if (uses[s] > 0) {
-      if (!mbar_wait(&bar[s], (uses[s] - 1) & 1, err)) ok = false;
+      if (!mbar_wait(&bar[s], (uses[s] - 1) & 1, err, nullptr)) ok = false;
     }
   tc_fence_after();
   if (ok && warp < 4) {
@@ -369,25 +256,7 @@ vc_tc_kernel(int64_t n, int d, int q, int Np, float alpha, const float *__restri
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-int g_err_alloc(int **p) {
-  static int *dev_err = nullptr;
-  if (!dev_err) {
-    if (cudaMalloc(&dev_err, sizeof(int)) != cudaSuccess) return GCGE_ENOMEM;
-    cudaMemset(dev_err, 0, sizeof(int));
-  }
-  *p = dev_err;
-  return GCGE_OK;
-}
 
-// Dynamic shared memory of one CTA, raised where needed so that the CTAs that fit
-// on one SM by shared memory never ask for more than the SM's 512 TMEM columns
-// (a CTA whose tcgen05.alloc cannot be served would stall until another exits).
-size_t tmem_limited_smem(size_t smem, uint32_t ncols) {
-  const size_t sm_bytes = 228 * 1024, per_cta_reserved = 1024;
-  const size_t by_tmem = 512 / ncols;
-  const size_t need = sm_bytes / (by_tmem + 1) + 1;
-  return std::max(smem, need > per_cta_reserved ? need - per_cta_reserved : smem);
-}
 size_t gram_tc_smem(int MT, int Np) {
   return tmem_limited_smem(2 * (2 * (size_t)MT * 128 * kKC * 4 + 2 * (size_t)Np * kKC * 4),
                            tmem_cols_for(MT * Np));
@@ -399,9 +268,27 @@ size_t vc_tc_smem(int Np) {
 
 }  // namespace
 
+// TMA-fed kernels of tc_tma.cu (GCGE_EINVAL: not applicable, use the staged kernels)
+int gram_tma(int64_t n, int m, int k, double alpha, const float *X, int64_t ldx, const float *Y,
+             int64_t ldy, double beta, double *C, int64_t ldc, Scratch &ws, cudaStream_t st);
+int vc_tma(int64_t n, int d, int q, double alpha, const float *V, int64_t ldv, const double *C,
+           int64_t ldc, double beta, float *Y, int64_t ldy, Scratch &ws, cudaStream_t st);
+
 // reduction kernel of blas.cu
 int gram_reduce_launch(int m, int k, int splits, const double *part, double alpha, double beta,
                        double *C, int64_t ldc, cudaStream_t st);
+
+namespace tc {
+int err_flag(int **p) {
+  static int *dev_err = nullptr;
+  if (!dev_err) {
+    if (cudaMalloc(&dev_err, sizeof(int)) != cudaSuccess) return GCGE_ENOMEM;
+    cudaMemset(dev_err, 0, sizeof(int));
+  }
+  *p = dev_err;
+  return GCGE_OK;
+}
+}  // namespace tc
 
 template <typename T>
 int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T *Y,
@@ -409,6 +296,10 @@ int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, cons
   if constexpr (sizeof(T) == 8) {
     return gram<T>(n, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, 0, ws, st);
   } else {
+    if (n > 0) {   // TMA-fed kernel first (any m, k); the staged kernel takes the rest
+      const int s = gram_tma(n, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, ws, st);
+      if (s != GCGE_EINVAL) return s;
+    }
     // up to 4 M-tiles of 128 and N <= 128 per launch; wider shapes are split
     const int mmax = 512, kmax = 128;
     if (m > mmax || k > kmax) {
@@ -423,7 +314,7 @@ int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, cons
     const int MT = (m + 127) / 128;
     const int Np = ((k + 15) / 16) * 16;
     int *err = nullptr;
-    GCGE_CHECK(g_err_alloc(&err));
+    GCGE_CHECK(tc::err_flag(&err));
     int64_t splits = 2 * (int64_t)device_sm_count();
     int64_t rps = round_up((n + splits - 1) / splits, kKC);
     if (rps < kKC) rps = kKC;
@@ -448,15 +339,19 @@ int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, cons
 
 template <typename T>
 int vc_tc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const double *C,
-          int64_t ldc, double beta, T *Y, int64_t ldy, cudaStream_t st) {
+          int64_t ldc, double beta, T *Y, int64_t ldy, cudaStream_t st, Scratch *ws) {
   if constexpr (sizeof(T) == 8) {
     return vc<T>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, 0, st);
   } else {
     if (d == 0) return vc<T>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, 0, st);   // Y = beta Y
+    if (ws) {   // TMA-fed kernel first; the staged kernel takes what it cannot address
+      const int s = vc_tma(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, *ws, st);
+      if (s != GCGE_EINVAL) return s;
+    }
     const int Np = std::min(256, ((q + 15) / 16) * 16);
     const int qt = (q + Np - 1) / Np;
     int *err = nullptr;
-    GCGE_CHECK(g_err_alloc(&err));
+    GCGE_CHECK(tc::err_flag(&err));
     const size_t smem = vc_tc_smem(Np);
     static size_t attr = 0;
     if (smem > attr) {
@@ -477,14 +372,14 @@ template int gram_tc<float>(int64_t, int, int, double, const float *, int64_t, c
 template int gram_tc<double>(int64_t, int, int, double, const double *, int64_t, const double *,
                              int64_t, double, double *, int64_t, Scratch &, cudaStream_t);
 template int vc_tc<float>(int64_t, int, int, double, const float *, int64_t, const double *,
-                          int64_t, double, float *, int64_t, cudaStream_t);
+                          int64_t, double, float *, int64_t, cudaStream_t, Scratch *);
 template int vc_tc<double>(int64_t, int, int, double, const double *, int64_t, const double *,
-                           int64_t, double, double *, int64_t, cudaStream_t);
+                           int64_t, double, double *, int64_t, cudaStream_t, Scratch *);
 
 // Device flag set by a tensor-core kernel whose bounded mbarrier wait timed out.
 int tc_error_flag(int *host_val, cudaStream_t st) {
   int *err = nullptr;
-  GCGE_CHECK(g_err_alloc(&err));
+  GCGE_CHECK(tc::err_flag(&err));
   GCGE_CUDA(cudaMemcpyAsync(host_val, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GCGE_CUDA(cudaStreamSynchronize(st));
   return GCGE_OK;

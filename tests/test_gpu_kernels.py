@@ -261,3 +261,65 @@ def test_random_block_matches_generator(g):
     torch.cuda.synchronize()
     ref = W.initial_block(n, k, 12345)
     assert np.abs(host(Xd)[:, :k] - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,m,k,offx,offy,ldx,ldy", [
+    (70001, 300, 150, 1, 3, 308, 156),   # 2 column groups of X, 2 of Y, unaligned bases
+    (4099, 40, 7, 2, 0, 44, 8),          # one tile, narrow Y
+    (129, 513, 1, 0, 1, 516, 4),         # few rows, 3 column groups, k = 1
+    (20011, 150, 33, 1, 1, 151, 35),     # leading dimensions not multiples of 4
+])
+def test_gram_f32_tc_layouts(g, n, m, k, offx, offy, ldx, ldy):
+    """Tensor-core Gram on sub-blocks of wider buffers (NaN outside the block)."""
+    import torch
+    rng = np.random.default_rng(n + m)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Y = rng.standard_normal((n, k)).astype(np.float32)
+    Xb = np.full((n, ldx), np.nan, np.float32)
+    Xb[:, offx:offx + m] = X
+    Yb = np.full((n, ldy), np.nan, np.float32)
+    Yb[:, offy:offy + k] = Y
+    Xd, Yd = dev(Xb), dev(Yb)
+    ldc = m + 2
+    Cd = torch.full((k, ldc), 5.0, dtype=torch.float64, device="cuda")   # col-major ldc x k
+    g.gcge_gram_f32(n, m, k, 1.5, Xd.data_ptr() + 4 * offx, ldx, Yd.data_ptr() + 4 * offy, ldy,
+                    0.5, Cd, ldc, tc=1)
+    torch.cuda.synchronize()
+    got = host(Cd).T
+    ref = 1.5 * (X.astype(np.float64).T @ Y.astype(np.float64)) + 2.5
+    bound = 1.5 * np.abs(X.astype(np.float64)).T @ np.abs(Y.astype(np.float64))
+    assert np.all(np.abs(got[:m] - ref) <= 2e-6 * bound + 1e-12)
+    assert np.all(got[m:] == 5.0)
+
+
+@pytest.mark.parametrize("n,d,q,offv,offy,ldv,ldy,beta", [
+    (70001, 37, 300, 3, 1, 44, 308, 0.5),     # 2 column groups of the result, unaligned
+    (1000, 200, 160, 0, 0, 200, 160, 0.0),
+    (257, 5, 20, 1, 2, 8, 24, -1.0),          # d below one K chunk
+    (33001, 120, 100, 1, 0, 121, 100, 0.0),   # ldv not a multiple of 4
+])
+def test_vc_f32_tc_layouts(g, n, d, q, offv, offy, ldv, ldy, beta):
+    """Tensor-core V C on sub-blocks of wider buffers (NaN outside the blocks)."""
+    import torch
+    rng = np.random.default_rng(n + d)
+    V = rng.standard_normal((n, d)).astype(np.float32)
+    Cm = rng.standard_normal((d, q))
+    Y0 = rng.standard_normal((n, q)).astype(np.float32)
+    Vb = np.full((n, ldv), np.nan, np.float32)
+    Vb[:, offv:offv + d] = V
+    Yb = np.full((n, ldy), np.nan, np.float32)
+    Yb[:, offy:offy + q] = Y0
+    Vd, Yd = dev(Vb), dev(Yb)
+    ldc = d + 3
+    Cbuf = np.full((q, ldc), np.nan)
+    Cbuf[:, :d] = Cm.T
+    g.gcge_vc_f32(n, d, q, 2.0, Vd.data_ptr() + 4 * offv, ldv, dev(Cbuf), ldc, beta,
+                  Yd.data_ptr() + 4 * offy, ldy, tc=1)
+    torch.cuda.synchronize()
+    got = host(Yd)
+    ref = 2.0 * (V.astype(np.float64) @ Cm) + beta * Y0.astype(np.float64)
+    bound = 2.0 * np.abs(V.astype(np.float64)) @ np.abs(Cm) + abs(beta) * np.abs(Y0)
+    assert np.all(np.abs(got[:, offy:offy + q] - ref) <= 2e-6 * bound + 1e-6)
+    mask = np.ones(got.shape, dtype=bool)
+    mask[:, offy:offy + q] = False
+    assert np.all(np.isnan(got[mask]))
