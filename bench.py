@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="no per-kernel CUDA-event profile (fewer API calls under ncu)")
+    ap.add_argument("--kernel-case", default=None,
+                    choices=["spmm32", "spmm64", "gram_tc", "vc_tc", "gram64", "vc64"],
+                    help="run one kernel class three times on the workload's shapes (for ncu)")
     return ap.parse_args()
 
 
@@ -138,6 +143,48 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# FP64 arithmetic peak of GB300 (nominal; the FP64 classes are bound by it, not by HBM)
+FP64_PEAK_TFLOPS = 1.25
+
+# DRAM traffic (read + write) over algorithmic bytes, per kernel class, from one full
+# ncu capture of each class on the q1_64 shapes (profiles/kernels_q1_64_shapes.md);
+# traffic per launch = this ratio x the class's algorithmic bytes per launch.
+TRAFFIC_RATIO = {"q1_64": {"spmm": 0.83, "gram": 1.02, "vc": 0.88, "spmm64": 0.98,
+                           "gram64": 1.01, "vc64": 3.30}}
+
+
+def traffic_per_launch(config, cls, prof):
+    r = TRAFFIC_RATIO.get(config, {}).get(cls)
+    if r is None or not prof or prof["calls"] == 0:
+        return None
+    return round(r * prof["bytes"] / prof["calls"])
+
+
+def kernel_rooflines(prof, hbm, src):
+    """Per kernel class: time share and achieved rate against its own roof."""
+    out = {}
+    for k, v in prof.items():
+        if k in ("syev", "other") or v["calls"] == 0 or v["ms"] <= 0:
+            continue
+        if k.endswith("64") and k != "spmm64":
+            ach = v["flops"] / (v["ms"] / 1e3) / 1e12
+            out[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": FP64_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                      "peak_source": "nominal FP64 rate"}
+        elif k == "spmm64" and v["flops"] / (v["ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS > \
+                v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm:
+            ach = v["flops"] / (v["ms"] / 1e3) / 1e12
+            out[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": FP64_PEAK_TFLOPS,
+                      "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                      "peak_source": "nominal FP64 rate"}
+        else:
+            ach = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                      "frac": round(ach / hbm, 4), "peak_source": src}
+        out[k].update(ms=round(v["ms"], 2), calls=int(v["calls"]))
+    return out
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -157,8 +204,9 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    def make(precision, profile=1):
-        return g.Solver(p.A, p.B, nev, bs, 1e-8, precision=precision, seed=0, profile=profile)
+    def make(precision):
+        return g.Solver(p.A, p.B, nev, bs, 1e-8, precision=precision, seed=0,
+                        profile=0 if args.no_profile else 1)
 
     def timed(solver, steps, warmup):
         for _ in range(warmup):
@@ -198,9 +246,11 @@ def run_ours(args, rank, world, local):
         ms_mx, prof_mx, launches_mx, its_mx, st_mx = timed(sm, args.steps, args.warmup)
         ev_mx, _ = g.gcge_eigenpairs(sm.h, nev, p.n, evd, True)
         sm.close()
-        s64 = make(g.GCGE_FP64)
-        ms_64, prof_64, launches_64, its_64, st_64 = timed(s64, args.fp64_steps, 1)
-        s64.close()
+        ms_64, its_64 = [float("nan")], [None]
+        if args.fp64_steps > 0:
+            s64 = make(g.GCGE_FP64)
+            ms_64, prof_64, launches_64, its_64, st_64 = timed(s64, args.fp64_steps, 1)
+            s64.close()
     clocks = clk.summary()
     # accuracy of the timed result against the closed-form spectrum
     import workloads as W
@@ -210,18 +260,21 @@ def run_ours(args, rank, world, local):
     t_mx = max_over_ranks(float(np.mean(ms_mx)) / 1e3, world)
     t_64 = max_over_ranks(float(np.mean(ms_64)) / 1e3, world)
 
-    # roofline of the dominant bandwidth kernel inside the timed mixed solves
+    # roofline of the dominant kernel class inside the timed mixed solves
     hbm, bf16, src = measured_peaks()
-    bw_classes = ["spmm", "gram", "vc", "cgvec"]
-    dom = max(bw_classes, key=lambda k: prof_mx[k]["ms"])
-    d = prof_mx[dom]
-    ach = d["bytes"] / (d["ms"] / 1e3) / 1e9 if d["ms"] > 0 else 0.0
+    kernels = kernel_rooflines(prof_mx, hbm, src)
+    if not kernels:   # --no-profile: no per-kernel times
+        kernels = {"none": {"bound": None, "achieved": None, "peak": None, "unit": None,
+                            "frac": None, "peak_source": None, "ms": 0.0, "calls": 0}}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
     spmm = prof_mx["spmm"]
     spmm_gbs = spmm["bytes"] / (spmm["ms"] / 1e3) / 1e9 if spmm["ms"] > 0 else 0.0
     tot_ms = sum(v["ms"] for v in prof_mx.values())
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
-            "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_source": src,
-            "traffic": None, "avg_launch_us": round(1e3 * d["ms"] / max(d["calls"], 1), 2)}
+    roof = {"bound": d["bound"], "kernel": dom, "achieved": d["achieved"], "peak": d["peak"],
+            "unit": d["unit"], "frac": d["frac"], "peak_source": d["peak_source"],
+            "traffic": traffic_per_launch(args.config, dom, prof_mx.get(dom)),
+            "avg_launch_us": round(1e3 * d["ms"] / max(d["calls"], 1), 2)}
     res.update(t_mx=t_mx, t_64=t_64)
 
     e2e = None
@@ -244,6 +297,7 @@ def run_ours(args, rank, world, local):
         "spmm_gbs": round(spmm_gbs, 1),
         "roofline": roof,
         "kernel_share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof_mx.items()} if tot_ms else {},
+        "kernels": kernels,
         "gpu_launches": int(launches_mx),
         "clocks": clocks,
     }
@@ -327,8 +381,53 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def kernel_case(args):
+    """Three launches of one kernel class on the benchmark workload's shapes, no timing:
+    the command that the committed ncu summaries capture."""
+    import torch
+    import paper_2111_06552_gb300 as g
+    g.lib()
+    p, nev, bs = workload(args.config)
+    n = p.n
+    torch.manual_seed(0)
+    rp = torch.tensor(p.A.indptr.astype(np.int32), device="cuda")
+    ci = torch.tensor(p.A.indices.astype(np.int32), device="cuda")
+    d, q, k = nev + 3 * bs + 2 * bs, nev + 3 * bs, bs   # RR basis width, X width, block
+    for _ in range(3):
+        if args.kernel_case in ("spmm32", "spmm64"):
+            dt = torch.float32 if args.kernel_case == "spmm32" else torch.float64
+            val = torch.tensor(p.A.data, device="cuda").to(dt)
+            X = torch.randn(n, k, device="cuda", dtype=dt)
+            Y = torch.empty(n, k, device="cuda", dtype=dt)
+            f = g.gcge_spmm_f32 if dt == torch.float32 else g.gcge_spmm_f64
+            f(n, rp, ci, val, k, 1.0, X, k, 0.0, Y, k)
+        elif args.kernel_case in ("gram_tc", "gram64"):
+            dt = torch.float32 if args.kernel_case == "gram_tc" else torch.float64
+            X = torch.randn(n, d, device="cuda", dtype=dt)
+            Y = torch.randn(n, k, device="cuda", dtype=dt)
+            C = torch.zeros(k, d, device="cuda", dtype=torch.float64)
+            if dt == torch.float32:
+                g.gcge_gram_f32(n, d, k, 1.0, X, d, Y, k, 0.0, C, d, tc=1)
+            else:
+                g.gcge_gram_f64(n, d, k, 1.0, X, d, Y, k, 0.0, C, d)
+        else:
+            dt = torch.float32 if args.kernel_case == "vc_tc" else torch.float64
+            V = torch.randn(n, d, device="cuda", dtype=dt)
+            Cm = torch.randn(q, d, device="cuda", dtype=torch.float64)
+            Z = torch.empty(n, q, device="cuda", dtype=dt)
+            if dt == torch.float32:
+                g.gcge_vc_f32(n, d, q, 1.0, V, d, Cm, d, 0.0, Z, q, tc=1)
+            else:
+                g.gcge_vc_f64(n, d, q, 1.0, V, d, Cm, d, 0.0, Z, q)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "n": n, "d": d, "q": q, "k": k}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        kernel_case(args)
+        return
     rank, world, local = dist_init(args.gpus)
     if args.impl == "reference":
         line = run_reference(args, rank, world)

@@ -87,13 +87,16 @@ typedef struct {
 } gcge_options;
 
 /* Kernel classes of the per-kernel profile in gcge_stats (profile = 1). */
-#define GCGE_K_SPMM 0         /* CSR x block products (SpMM), incl. the CG SpMM + dot     */
-#define GCGE_K_GRAM 1         /* tall-skinny Gram X^T Y                                   */
-#define GCGE_K_VC 2           /* block update V C                                         */
+#define GCGE_K_SPMM 0         /* FP32 CSR x block products (SpMM), incl. the CG SpMM + dot */
+#define GCGE_K_GRAM 1         /* FP32 tall-skinny Gram X^T Y (tensor cores)               */
+#define GCGE_K_VC 2           /* FP32 block update V C (tensor cores)                     */
 #define GCGE_K_SYEV 3         /* dense Rayleigh-Ritz / leaf eigensolves                   */
 #define GCGE_K_CGVEC 4        /* CG vector updates and reductions                         */
 #define GCGE_K_OTHER 5        /* copies, residual reductions, small dense kernels         */
-#define GCGE_K_CLASSES 6
+#define GCGE_K_SPMM64 6       /* FP64 SpMM                                                */
+#define GCGE_K_GRAM64 7       /* FP64 Gram                                                */
+#define GCGE_K_VC64 8         /* FP64 V C                                                 */
+#define GCGE_K_CLASSES 9
 
 /* Per-solve statistics (times are CUDA-event milliseconds on the handle's stream). */
 typedef struct {
@@ -110,10 +113,10 @@ typedef struct {
   int64_t kernel_launches;  /* kernels launched by the library during the solve       */
   /* per kernel class (GCGE_K_*), filled when options.profile = 1: summed CUDA-event
    * time of the launches, their count, and their algorithmic bytes and flops */
-  double prof_ms[8];
-  int64_t prof_calls[8];
-  double prof_bytes[8];
-  double prof_flops[8];
+  double prof_ms[12];
+  int64_t prof_calls[12];
+  double prof_bytes[12];
+  double prof_flops[12];
 } gcge_stats;
 
 /* ----------------------------------------------------------------- solver */

@@ -34,7 +34,7 @@ GCGE_ENAN = -7
 GCGE_ENOTREADY = -8
 GCGE_FP64 = 0
 GCGE_MIXED = 1
-KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other")
+KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other", "spmm64", "gram64", "vc64")
 
 
 class GcgeError(RuntimeError):
@@ -63,9 +63,9 @@ class gcge_stats(C.Structure):
                 ("cg_steps", C.c_int64), ("moves", C.c_int), ("ms_total", C.c_double),
                 ("ms_step", C.c_double * 7), ("ms_syev", C.c_double),
                 ("max_orth_err", C.c_double), ("max_abar_err", C.c_double),
-                ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 8),
-                ("prof_calls", C.c_int64 * 8), ("prof_bytes", C.c_double * 8),
-                ("prof_flops", C.c_double * 8)]
+                ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 12),
+                ("prof_calls", C.c_int64 * 12), ("prof_bytes", C.c_double * 12),
+                ("prof_flops", C.c_double * 12)]
 
 
 _P = C.c_void_p

@@ -328,7 +328,7 @@ static int cg_loop(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, 
   }
   for (int it = 0; it < max_iter; ++it) {
     {
-      ProfScope ps(prof, GCGE_K_SPMM, spmm_bytes, 2.0 * nnzS * k);
+      ProfScope ps(prof, sizeof(T) == 8 ? GCGE_K_SPMM64 : GCGE_K_SPMM, spmm_bytes, 2.0 * nnzS * k);
       GCGE_CHECK(launch_spmm<T>(n, rp, ci, S, k, T(1), w.p, ld, T(0), w.q, ld, w.pq, w.nbcap, st,
                                 w.part_a, w.tickets));
     }

@@ -15,8 +15,8 @@ struct KProf {
   };
   std::vector<Slot> pool;
   size_t used = 0;
-  double ms[8] = {0}, bytes[8] = {0}, flops[8] = {0};
-  int64_t calls[8] = {0};
+  double ms[12] = {0}, bytes[12] = {0}, flops[12] = {0};
+  int64_t calls[12] = {0};
 
   ~KProf() {
     harvest();

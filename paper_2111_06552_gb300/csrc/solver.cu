@@ -410,28 +410,33 @@ class Engine {
   }
   int spA(const T *X, int64_t ldx, int k, T *Y, int64_t ldy) {
     g_launches += 1;
-    ProfScope ps(prof, GCGE_K_SPMM, spmm_bytes(h_->A, k), 2.0 * h_->A.nnz * k);
+    ProfScope ps(prof, cls(GCGE_K_SPMM), spmm_bytes(h_->A, k), 2.0 * h_->A.nnz * k);
     return launch_spmm<T>(n_, h_->A.rp, h_->A.ci, csr_vals<T>(h_->A), k, T(1), X, ldx, T(0), Y,
                           ldy, nullptr, 0, st_);
   }
   int spB(const T *X, int64_t ldx, int k, T *Y, int64_t ldy) {
     g_launches += 1;
     if (bI_) return copyT(k, X, ldx, Y, ldy);
-    ProfScope ps(prof, GCGE_K_SPMM, spmm_bytes(h_->B, k), 2.0 * h_->B.nnz * k);
+    ProfScope ps(prof, cls(GCGE_K_SPMM), spmm_bytes(h_->B, k), 2.0 * h_->B.nnz * k);
     return launch_spmm<T>(n_, h_->B.rp, h_->B.ci, csr_vals<T>(h_->B), k, T(1), X, ldx, T(0), Y,
                           ldy, nullptr, 0, st_);
   }
   int use_tc() const;
+  // profile class of an FP32 kernel kind, or its FP64 counterpart in the FP64 engine
+  static int cls(int c) {
+    if (sizeof(T) == 4) return c;
+    return c == GCGE_K_SPMM ? GCGE_K_SPMM64 : c == GCGE_K_GRAM ? GCGE_K_GRAM64 : GCGE_K_VC64;
+  }
   int gramT(int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
             double beta, double *C, int64_t ldc) {
     g_launches += 2;
-    ProfScope ps(prof, GCGE_K_GRAM, (double)n_ * (m + k) * sizeof(T), 2.0 * n_ * m * k);
+    ProfScope ps(prof, cls(GCGE_K_GRAM), (double)n_ * (m + k) * sizeof(T), 2.0 * n_ * m * k);
     return gram<T>(n_, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, use_tc(), ws_, st_);
   }
   int vcT(int d, int q, double alpha, const T *V, int64_t ldv, const double *C, int64_t ldc,
           double beta, T *Y, int64_t ldy) {
     g_launches += 1;
-    ProfScope ps(prof, GCGE_K_VC, (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T),
+    ProfScope ps(prof, cls(GCGE_K_VC), (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T),
                  2.0 * n_ * d * q);
     return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc(), st_, &ws_);
   }

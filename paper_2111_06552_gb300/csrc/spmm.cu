@@ -10,6 +10,11 @@
 // a whole row's worth of FMAs and keeps many independent gathers in flight; the
 // nonzero loop is unrolled by four.
 //
+// Each CTA walks one contiguous block of rows, 256 / G rows at a time, with two CTAs
+// per SM: consecutive rows of a banded (stencil / FEM) matrix gather mostly the same
+// rows of X, which then stay in L1 between the CTA's steps instead of being fetched
+// from L2 once per nonzero.
+//
 // Optional fused epilogue (used by the CG step): per column j the dot product
 // sum_i X[i, j] (A X)[i, j].  Lanes holding the same columns reduce over the rows of
 // the warp with shuffles, then over the CTA in shared memory; every CTA writes one
@@ -52,7 +57,7 @@ __global__ void __launch_bounds__(kSpmmThreads)
 spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const T *__restrict__ val, int k, int G, T alpha, const T *__restrict__ X,
             int64_t ldx, T beta, T *__restrict__ Y, int64_t ldy, double *__restrict__ part,
-            double *__restrict__ dot_out, unsigned *__restrict__ ticket) {
+            double *__restrict__ dot_out, unsigned *__restrict__ ticket, int64_t rows_per_cta) {
   extern __shared__ double sdot[];   // k column sums, then blockDim.x reduction scratch
   const int nchunks = (k + VEC - 1) / VEC;
   const int full = k / VEC;                 // chunks that are complete
@@ -62,15 +67,16 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     for (int j = threadIdx.x; j < k; j += blockDim.x) sdot[j] = 0.0;
     __syncthreads();
   }
-  const int64_t rows_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-       row - (threadIdx.x / G) < n; row += rows_per_grid) {
+  const int64_t rows_per_step = blockDim.x / G;
+  const int64_t blk_end = min(n, (int64_t)(blockIdx.x + 1) * rows_per_cta);
+  for (int64_t row = (int64_t)blockIdx.x * rows_per_cta + threadIdx.x / G;
+       row - (threadIdx.x / G) < blk_end; row += rows_per_step) {
     T acc[NV][VEC];
 #pragma unroll
     for (int c = 0; c < NV; ++c)
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[c][v] = T(0);
-    const bool live = row < n;
+    const bool live = row < blk_end;
     if (live) {
       const int beg = __ldg(rp + row), end = __ldg(rp + row + 1);
       int e = beg;
@@ -161,6 +167,7 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
 
 struct Plan {
   int vec, G, nv, grid;
+  int64_t rows_per_cta;
 };
 
 template <typename T>
@@ -171,24 +178,37 @@ Plan plan_for(int64_t n, int k, bool aligned) {
   while ((chunks + G - 1) / G > 8 && G < 32) G <<= 1;
   int nv = (chunks + G - 1) / G;
   if (nv > 8) nv = 8;           // k > 32 * 8 * vec: the caller splits the columns
-  const int64_t threads = n * G;
-  int64_t grid = (threads + kSpmmThreads - 1) / kSpmmThreads;
-  const int64_t cap = (int64_t)device_sm_count() * 8;   // full occupancy, grid-stride beyond
+  const int64_t step = kSpmmThreads / G;   // rows per CTA step
+  int64_t grid = (n + step - 1) / step;
+  const int64_t cap = (int64_t)device_sm_count() * 2;   // two contiguous row streams per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  return {vec, G, nv, (int)grid};
+  int64_t rpc = (n + grid - 1) / grid;
+  rpc = ((rpc + step - 1) / step) * step;
+  grid = (n + rpc - 1) / rpc;
+  if (grid < 1) grid = 1;
+  return {vec, G, nv, (int)grid, rpc};
 }
 
 template <typename T, int VEC, int NV>
 void launch_v(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, const T *val,
               int k, T alpha, const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *part,
               double *dot_out, unsigned *ticket, cudaStream_t st) {
+  static bool carveout = false;   // X rows are re-read through L1: prefer L1 over shared
+  if (!carveout) {
+    cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, true>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, false>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carveout = true;
+  }
   if (dot_out)
     spmm_kernel<T, VEC, NV, true><<<pl.grid, kSpmmThreads, (k + kSpmmThreads) * sizeof(double), st>>>(
-        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket);
+        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, pl.rows_per_cta);
   else
     spmm_kernel<T, VEC, NV, false><<<pl.grid, kSpmmThreads, 0, st>>>(
-        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, nullptr, nullptr, nullptr);
+        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, nullptr, nullptr, nullptr,
+        pl.rows_per_cta);
 }
 
 template <typename T, int VEC>
