@@ -79,7 +79,7 @@ typedef struct {
   int max_iter;             /* GCG iterations (Rayleigh-Ritz solves) before ENOTCONV (2000) */
   uint64_t seed;            /* initial block N(0,1) from splitmix64 + Box-Muller      (0)   */
   const double *initial_block; /* optional host n x size_x row-major start block (NULL) */
-  double mixed_switch_tol;  /* MIXED: FP32 phase ends at this relative residual     (1e-5) */
+  double mixed_switch_tol;  /* MIXED: FP32 phase ends at this relative residual     (3e-6) */
   int verbose;              /* 1: one line per iteration on stderr                    (0)   */
   int checks;               /* 1: per iteration compare the structured Rayleigh-Ritz  (0)
                                matrix with an explicit V^T A V and V^T B V with I (slow) */

@@ -172,7 +172,7 @@ int gcge_options_default(gcge_options *o) {
   o->max_iter = 2000;
   o->seed = 0;
   o->initial_block = nullptr;
-  o->mixed_switch_tol = 1e-5;
+  o->mixed_switch_tol = 3e-6;
   o->verbose = 0;
   o->checks = 0;
   o->profile = 0;

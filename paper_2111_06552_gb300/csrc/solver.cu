@@ -308,7 +308,8 @@ class Engine {
   bool checks = false;
   bool stagnated = false;
   int stagnation_limit = 0;   // > 0: stop after this many iterations without a new lock
-                              // or a halving of the first unconverged residual
+                              // or progress of the first unconverged column (a 10% gain
+                              // on its best residual, or a falling Ritz value)
   KProf *prof = nullptr;      // per-kernel-class event profile (null: off)
   bool cg_fp32 = false;       // FP64 engine: run the inner CG in FP32 on the FP64 residual
   bool use_p = true;          // build P (STEP 5); the refinement phase may go without it
@@ -954,6 +955,7 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
   bool first = true;
   int since_lock = 0;            // iterations without a new lock and without progress
   double best_res = 1e300;       // best residual of the first unconverged column
+  double prev_lam = 1e300;       // its Ritz value in the previous iteration
   while (true) {
     ++it_;
     const int d = kx_ + np_ + nw_;
@@ -990,11 +992,19 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
       nlock_ += c;
       since_lock = 0;
       best_res = 1e300;
-    } else if (first_res_ < 0.5 * best_res) {   // still converging: not stagnant
-      best_res = first_res_;
-      since_lock = 0;
+      prev_lam = 1e300;
     } else {
-      ++since_lock;
+      // progress: the residual of the first unconverged column gains 10% on its best, or
+      // its Ritz value still falls (the start block is far from the eigenvector)
+      const double lam_first = (size_t)c < lam_h_.size() ? lam_h_[c] : 0.0;
+      const bool falling = lam_first < prev_lam - 1e-6 * std::fabs(lam_first);
+      if (first_res_ < 0.9 * best_res || falling) {
+        best_res = std::min(best_res, first_res_);
+        since_lock = 0;
+      } else {
+        ++since_lock;
+      }
+      prev_lam = lam_first;
     }
     toc(4);
     if (h_->opt.verbose)
@@ -1230,7 +1240,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     Engine<double> e2(h, h->tol, std::max(1, h->opt.max_iter - it1));
     e2.checks = h->opt.checks != 0;
     e2.cg_fp32 = true;
-    e2.use_p = false;
+    e2.use_p = h->moving;   // the moving mechanism regrows its window from P and W
     if (h->opt.profile) e2.prof = &prof;
     s = e2.setup(sx, h->nev, h->store_cap, bs2);
     if (s == GCGE_OK) {
