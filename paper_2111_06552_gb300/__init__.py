@@ -55,7 +55,8 @@ class gcge_options(C.Structure):
                 ("use_shift", C.c_int), ("orth_leaf", C.c_int), ("moving", C.c_int),
                 ("size_x", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("initial_block", C.c_void_p), ("mixed_switch_tol", C.c_double),
-                ("verbose", C.c_int), ("checks", C.c_int), ("profile", C.c_int)]
+                ("verbose", C.c_int), ("checks", C.c_int), ("profile", C.c_int),
+                ("mixed_bs2", C.c_int)]
 
 
 class gcge_stats(C.Structure):

@@ -173,6 +173,7 @@ int gcge_options_default(gcge_options *o) {
   o->seed = 0;
   o->initial_block = nullptr;
   o->mixed_switch_tol = 3e-6;
+  o->mixed_bs2 = 0;
   o->verbose = 0;
   o->checks = 0;
   o->profile = 0;
@@ -193,7 +194,7 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
     h->opt = *opt;
   else
     gcge_options_default(&h->opt);
-  if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 ||
+  if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 || h->opt.mixed_bs2 < 0 ||
       (h->opt.precision != GCGE_FP64 && h->opt.precision != GCGE_MIXED)) {
     delete h;
     return GCGE_EINVAL;

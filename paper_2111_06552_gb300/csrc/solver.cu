@@ -1232,11 +1232,12 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
   *iters32 = it1;
   int s;
   {
-    // phase 2: FP64 iteration started from the phase-1 vectors; without the moving
-    // mechanism every wanted column is active at once (block size nev), with it the
-    // window of size_x is refilled from the phase-1 vectors as pairs lock.  The inexact
-    // inner CG runs in FP32 on the FP64 residual; no P.
-    const int bs2 = h->moving ? h->bs : std::min(h->nev, sx);
+    // phase 2: FP64 iteration started from the phase-1 vectors (active block blockSize
+    // unless mixed_bs2 says otherwise); with the moving mechanism the window of size_x
+    // is refilled from the phase-1 vectors as pairs lock, and P is built.  The inexact
+    // inner CG runs in FP32 on the FP64 residual.
+    int bs2 = std::min(h->bs, sx);
+    if (h->opt.mixed_bs2 > 0) bs2 = std::min(h->opt.mixed_bs2, sx);
     Engine<double> e2(h, h->tol, std::max(1, h->opt.max_iter - it1));
     e2.checks = h->opt.checks != 0;
     e2.cg_fp32 = true;

@@ -4,14 +4,15 @@
 // gathers the contiguous k-vector X[j, 0:k].  The k columns are cut into 16-byte
 // chunks (4 floats or 2 doubles) when the block is 16-byte aligned, else into single
 // elements.  A group of G lanes owns one row; lane l of the group holds chunks
-// l, l+G, ... (at most NV of them) in registers, so for the block widths of the
-// method (k = 2..100) a row needs 1..8 lanes and a warp works on 4..32 rows at once.
+// l, l+G, ... (at most two of them when k allows) in registers, so for the block
+// widths of the method (k = 2..100) a row needs 1..16 lanes and a warp works on 2..32
+// rows at once.
 // This keeps the per-nonzero instruction overhead (index, value, address) shared by
 // a whole row's worth of FMAs and keeps many independent gathers in flight; the
 // nonzero loop is unrolled by four.
 //
-// Each CTA walks one contiguous block of rows, 256 / G rows at a time, with two CTAs
-// per SM: consecutive rows of a banded (stencil / FEM) matrix gather mostly the same
+// Each CTA walks one contiguous block of rows, 256 / G rows at a time, with two to four
+// CTAs per SM: consecutive rows of a banded (stencil / FEM) matrix gather mostly the same
 // rows of X, which then stay in L1 between the CTA's steps instead of being fetched
 // from L2 once per nonzero.
 //
@@ -175,12 +176,16 @@ Plan plan_for(int64_t n, int k, bool aligned) {
   const int vec = aligned ? (int)(16 / sizeof(T)) : 1;
   const int chunks = (k + vec - 1) / vec;
   int G = 1;
-  while ((chunks + G - 1) / G > 8 && G < 32) G <<= 1;
+  // FP32 blocks up to 32 columns: at most two 16-byte chunks per lane (short register
+  // footprint, four CTAs per SM); otherwise up to eight chunks per lane, two CTAs per SM
+  const bool narrow = sizeof(T) == 4 && k <= 32;
+  const int cpl = narrow ? 2 : 8;
+  while ((chunks + G - 1) / G > cpl && G < 32) G <<= 1;
   int nv = (chunks + G - 1) / G;
   if (nv > 8) nv = 8;           // k > 32 * 8 * vec: the caller splits the columns
   const int64_t step = kSpmmThreads / G;   // rows per CTA step
   int64_t grid = (n + step - 1) / step;
-  const int64_t cap = (int64_t)device_sm_count() * 2;   // two contiguous row streams per SM
+  const int64_t cap = (int64_t)device_sm_count() * (narrow ? 4 : 2);   // row streams per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   int64_t rpc = (n + grid - 1) / grid;

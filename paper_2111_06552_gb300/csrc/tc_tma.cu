@@ -48,6 +48,10 @@ constexpr int kGRows = 32;      // K rows per chunk (4 MMA k-steps of 8)
 constexpr int kGXBox = 132;     // X box: 128 columns + up to 3 leading, 16-byte multiple
 constexpr int kGThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 convert + epilogue
 constexpr int kGConv = 256;     // converter threads
+// FP32 accumulation window: the tensor memory accumulator is drained into the FP64
+// partial sums every 16 chunks (512 rows; 32 chunks when Y is wider than 32 columns),
+// so rounding in the FP32 accumulator stays at the level of a 512- or 1024-term sum
+// however many rows one CTA covers.
 constexpr int kMaxStages = 8;   // shared-memory stages (runtime count <= this)
 constexpr int kMaxA = 4;        // tensor-memory A-operand stages (runtime count <= this)
 constexpr uint32_t kSmemBudget = 224 * 1024;   // + alignment slack + static
@@ -86,7 +90,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
                 int64_t rps, double *__restrict__ part, int *__restrict__ err) {
   extern __shared__ unsigned char smraw[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], afull[kMaxA],
-      aempty[kMaxA], dfull;
+      aempty[kMaxA], dfull, dflush, dread;
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
@@ -100,6 +104,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
   const int64_t r0 = (int64_t)blockIdx.x * rps;
   const int64_t r1 = min(n, r0 + rps);
   const int nch = (int)((r1 - r0 + kGRows - 1) / kGRows);
+  const int kGWin = Np <= 32 ? 16 : 32;
   const uint32_t ncols = 512 / cps;
   const uint32_t xbytes = kGXBox * kGRows * 4, ybytes = (uint32_t)bk * kGRows * 4;
 
@@ -114,6 +119,8 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
       mbar_init(&aempty[s], 1);
     }
     mbar_init(&dfull, 1);
+    mbar_init(&dflush, 1);
+    mbar_init(&dread, kGConv);
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -146,7 +153,12 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
     const uint32_t id2 = idesc_tf32(128, 2 * Np), id1 = idesc_tf32(128, Np);
     for (int c = 0; c < nch; ++c) {
       const int ts = c % nA, v = c / nA;
+      const int cw = c % kGWin, wi = c / kGWin;
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(&afull[ts], v & 1, err, ab))) break;
+      // a new window overwrites the accumulator: the previous one must have been read
+      if (cw == 0 && wi > 0 &&
+          !__all_sync(0xFFFFFFFFu, mbar_wait(&dread, (wi - 1) & 1, err, ab)))
+        break;
       tc_fence_after();
       const uint32_t bb = su32(sm + L.braw + ts * L.bstage);
 #pragma unroll
@@ -155,7 +167,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
         for (int t = 0; t < MTg; ++t) {
           const uint32_t ah = tmem + abase + (ts * MT + t) * 64 + ks * 8, al = ah + 32;
           const uint32_t d1 = tmem + t * 3 * Np, d2 = d1 + 2 * Np;
-          const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+          const uint32_t acc = (cw > 0 || ks > 0) ? 1u : 0u;
           if (leader) {
             mma_ts(d1, ah, bd, id2, acc);   // X_hi^T [Y_hi | Y_lo]
             mma_ts(d2, al, bd, id1, acc);   // X_lo^T Y_hi (first Np rows of B)
@@ -163,7 +175,10 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
         }
       }
       __syncwarp();
-      if (leader) mma_commit(&aempty[ts]);
+      if (leader) {
+        mma_commit(&aempty[ts]);
+        if (cw == kGWin - 1 || c == nch - 1) mma_commit(&dflush);
+      }
       __syncwarp();
     }
     if (leader) {
@@ -217,24 +232,40 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(&afull[ts]);
-    }
-    const bool done = mbar_wait(&dfull, 0, err, ab);
-    tc_fence_after();
-    if (ok && done && !*ab) {
-      double *pp = part + (int64_t)blockIdx.x * m * k;
-      for (int t = 0; t < MTg; ++t) {
-        const int i = i0 + 128 * t + 32 * q + lane;
-        const uint32_t d1 = tmem + lane_addr + t * 3 * Np;
-        for (int jb = hs * 8; jb < Np; jb += 16) {
-          float a1[8], a2[8], a3[8];
-          tmem_ld8(d1 + jb, a1);
-          tmem_ld8(d1 + Np + jb, a2);
-          tmem_ld8(d1 + 2 * Np + jb, a3);
+      if ((c % kGWin) == kGWin - 1 || c == nch - 1) {
+        // drain this window's accumulator: this thread's row of every M tile, its half of
+        // the columns (at most 8 groups of 8), then add into the FP64 partial sums
+        const int wi = c / kGWin;
+        if (!mbar_wait(&dflush, wi & 1, err, ab)) { ok = false; break; }
+        tc_fence_after();
+        float acc[8][8];
+        int slot = 0;
+        for (int t = 0; t < MTg; ++t) {
+          const uint32_t d1 = tmem + lane_addr + t * 3 * Np;
+          for (int jb = hs * 8; jb < Np && slot < 8; jb += 16, ++slot) {
+            float a1[8], a2[8], a3[8];
+            tmem_ld8(d1 + jb, a1);
+            tmem_ld8(d1 + Np + jb, a2);
+            tmem_ld8(d1 + 2 * Np + jb, a3);
 #pragma unroll
-          for (int uu = 0; uu < 8; ++uu) {
-            const int j = jb + uu;
-            if (i < m && j < kw)
-              pp[(int64_t)(j0 + j) * m + i] = (double)a1[uu] + (double)a2[uu] + (double)a3[uu];
+            for (int uu = 0; uu < 8; ++uu) acc[slot][uu] = a1[uu] + a2[uu] + a3[uu];
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&dread);
+        double *pp = part + (int64_t)blockIdx.x * m * k;
+        slot = 0;
+        for (int t = 0; t < MTg; ++t) {
+          const int i = i0 + 128 * t + 32 * q + lane;
+          for (int jb = hs * 8; jb < Np && slot < 8; jb += 16, ++slot) {
+#pragma unroll
+            for (int uu = 0; uu < 8; ++uu) {
+              const int j = jb + uu;
+              if (i < m && j < kw) {
+                double *pj = pp + (int64_t)(j0 + j) * m + i;
+                *pj = (wi == 0 ? 0.0 : *pj) + (double)acc[slot][uu];
+              }
+            }
           }
         }
       }
