@@ -149,7 +149,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic (read + write) over algorithmic bytes, per kernel class, from one full
 # ncu capture of each class on the q1_64 shapes (profiles/kernels_q1_64_shapes.md);
 # traffic per launch = this ratio x the class's algorithmic bytes per launch.
-TRAFFIC_RATIO = {"q1_64": {"spmm": 0.83, "gram": 1.02, "vc": 0.88, "spmm64": 0.98,
+TRAFFIC_RATIO = {"q1_64": {"spmm": 0.84, "gram": 1.05, "vc": 0.88, "spmm64": 0.98,
                            "gram64": 1.01, "vc64": 3.30}}
 
 

@@ -323,3 +323,20 @@ def test_vc_f32_tc_layouts(g, n, d, q, offv, offy, ldv, ldy, beta):
     mask = np.ones(got.shape, dtype=bool)
     mask[:, offy:offy + q] = False
     assert np.all(np.isnan(got[mask]))
+
+
+def test_gram_f32_tc_long_rows(g):
+    """Tensor-core Gram over 2^21 rows of non-zero-mean data: the FP32 accumulator is
+    drained into FP64 in windows, so the error stays at FP32-product level instead of
+    growing with the rows one CTA covers."""
+    import torch
+    n, m, k = 2097152, 40, 40
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn(n, m, device="cuda", generator=gen) + 0.5
+    Y = torch.randn(n, k, device="cuda", generator=gen) + 0.5
+    C = torch.zeros(k, m, dtype=torch.float64, device="cuda")
+    g.gcge_gram_f32(n, m, k, 1.0, X, m, Y, k, 0.0, C, m, tc=1)
+    torch.cuda.synchronize()
+    ref = X.double().T @ Y.double()
+    bound = X.double().abs().T @ Y.double().abs()
+    assert ((C.T - ref).abs() / bound).max().item() <= 2e-6
