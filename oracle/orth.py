@@ -39,7 +39,7 @@ from .linalg import spmm, b_norms, sym_eig
 class OrthParams:
     defl_tol: float = 1e-12
     defl_max: int = 3
-    drop_tol: float = 1e-10
+    drop_tol: float = 1e-13
     leaf_tol: float = 1e-12
     leaf_max: int = 3
     leaf_drop: float = 1e-20

@@ -194,7 +194,8 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
     h->opt = *opt;
   else
     gcge_options_default(&h->opt);
-  if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 || h->opt.mixed_bs2 < 0 ||
+  if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 ||
+      h->opt.mixed_bs2 < 0 ||
       (h->opt.precision != GCGE_FP64 && h->opt.precision != GCGE_MIXED)) {
     delete h;
     return GCGE_EINVAL;

@@ -240,7 +240,7 @@ template <typename T>
 Thresholds thresholds();
 template <>
 Thresholds thresholds<double>() {
-  return {1e-12, 1e-10, 1e-12, 1e-20, 1e-12, 1e-10, 1e-14, 3, 3, 3};
+  return {1e-12, 1e-13, 1e-12, 1e-20, 1e-12, 1e-10, 1e-14, 3, 3, 3};
 }
 template <>
 Thresholds thresholds<float>() {

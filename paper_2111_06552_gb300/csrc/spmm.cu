@@ -81,13 +81,25 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     if (live) {
       const int beg = __ldg(rp + row), end = __ldg(rp + row + 1);
       int e = beg;
-      for (; e + 3 < end; e += 4) {
-        int cc[4];
-        T vv[4];
+      // groups of four nonzeros; the next group's indices and values are loaded before
+      // this group's gathers, so their latency overlaps instead of adding up
+      int cc[4], cn[4];
+      T vv[4], vn[4];
+      if (e + 3 < end) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           cc[u] = __ldg(ci + e + u);
           vv[u] = __ldg(val + e + u);
+        }
+      }
+      for (; e + 3 < end; e += 4) {
+        const bool more = e + 7 < end;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            cn[u] = __ldg(ci + e + 4 + u);
+            vn[u] = __ldg(val + e + 4 + u);
+          }
         }
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
@@ -106,6 +118,13 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             for (int u = 0; u < 4; ++u)
               for (int v = 0; v < VEC && ch * VEC + v < k; ++v)
                 acc[c][v] += vv[u] * __ldg(X + (int64_t)cc[u] * ldx + ch * VEC + v);
+          }
+        }
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            cc[u] = cn[u];
+            vv[u] = vn[u];
           }
         }
       }

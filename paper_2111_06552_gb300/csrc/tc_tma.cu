@@ -104,7 +104,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
   const int64_t r0 = (int64_t)blockIdx.x * rps;
   const int64_t r1 = min(n, r0 + rps);
   const int nch = (int)((r1 - r0 + kGRows - 1) / kGRows);
-  const int kGWin = Np <= 32 ? 16 : 32;
+  const int win = Np <= 32 ? 16 : 32;   // chunks per FP32 accumulation window
   const uint32_t ncols = 512 / cps;
   const uint32_t xbytes = kGXBox * kGRows * 4, ybytes = (uint32_t)bk * kGRows * 4;
 
@@ -153,7 +153,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
     const uint32_t id2 = idesc_tf32(128, 2 * Np), id1 = idesc_tf32(128, Np);
     for (int c = 0; c < nch; ++c) {
       const int ts = c % nA, v = c / nA;
-      const int cw = c % kGWin, wi = c / kGWin;
+      const int cw = c % win, wi = c / win;
       if (!__all_sync(0xFFFFFFFFu, mbar_wait(&afull[ts], v & 1, err, ab))) break;
       // a new window overwrites the accumulator: the previous one must have been read
       if (cw == 0 && wi > 0 &&
@@ -177,7 +177,7 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
       __syncwarp();
       if (leader) {
         mma_commit(&aempty[ts]);
-        if (cw == kGWin - 1 || c == nch - 1) mma_commit(&dflush);
+        if (cw == win - 1 || c == nch - 1) mma_commit(&dflush);
       }
       __syncwarp();
     }
@@ -232,10 +232,10 @@ gram_tma_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__
       fence_async_smem();
       tc_fence_before();
       mbar_arrive(&afull[ts]);
-      if ((c % kGWin) == kGWin - 1 || c == nch - 1) {
+      if ((c % win) == win - 1 || c == nch - 1) {
         // drain this window's accumulator: this thread's row of every M tile, its half of
         // the columns (at most 8 groups of 8), then add into the FP64 partial sums
-        const int wi = c / kGWin;
+        const int wi = c / win;
         if (!mbar_wait(&dflush, wi & 1, err, ab)) { ok = false; break; }
         tc_fence_after();
         float acc[8][8];
