@@ -84,8 +84,7 @@ typedef struct {
   int checks;               /* 1: per iteration compare the structured Rayleigh-Ritz  (0)
                                matrix with an explicit V^T A V and V^T B V with I (slow) */
   int profile;              /* 1: time every kernel class with CUDA events           (0)   */
-  int mixed_bs2;            /* MIXED: active block width of the FP64 phase; 0: blockSize (0)
-                               if phase 1 locked every pair (or moving), else nev */
+  int mixed_bs2;            /* MIXED: active block width of the FP64 phase; 0: blockSize (0) */
 } gcge_options;
 
 /* Kernel classes of the per-kernel profile in gcge_stats (profile = 1). */
