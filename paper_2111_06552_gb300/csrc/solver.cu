@@ -1201,6 +1201,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
   int nz = 0;
   const int64_t ldz = round_up(h->store_cap, 4);
   int it1 = 0;
+  bool p1_all = false;   // phase 1 locked every wanted pair
   {
     Engine<float> e1(h, std::max(h->opt.mixed_switch_tol, h->tol), h->opt.max_iter);
     e1.stagnation_limit = 10;
@@ -1213,6 +1214,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     GCGE_CHECK(tc_error_flag(&tc_err, h->st));
     if (tc_err) return GCGE_ETIMEOUT;
     it1 = e1.iterations();
+    p1_all = e1.nlock() >= h->nev;
     add_stats(h, e1);
     const int take_s = std::min(e1.nlock(), h->store_cap);
     const int take_x = std::min(e1.kx(), h->store_cap - take_s);
@@ -1234,14 +1236,17 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
   {
     // phase 2: FP64 iteration started from the phase-1 vectors (active block blockSize
     // unless mixed_bs2 says otherwise); with the moving mechanism the window of size_x
-    // is refilled from the phase-1 vectors as pairs lock, and P is built.  The inexact
-    // inner CG runs in FP32 on the FP64 residual.
+    // is refilled from the phase-1 vectors as pairs lock.  The inexact inner CG runs
+    // in FP32 on the FP64 residual.
     int bs2 = std::min(h->bs, sx);
     if (h->opt.mixed_bs2 > 0) bs2 = std::min(h->opt.mixed_bs2, sx);
     Engine<double> e2(h, h->tol, std::max(1, h->opt.max_iter - it1));
     e2.checks = h->opt.checks != 0;
     e2.cg_fp32 = true;
-    e2.use_p = h->moving;   // the moving mechanism regrows its window from P and W
+    // when phase 1 reached the switch tolerance on every pair, phase 2 is a short
+    // refinement and P does not pay for itself; otherwise it is a full FP64 solve
+    // and P (STEP 5) is built as in the plain path
+    e2.use_p = h->moving || !p1_all;
     if (h->opt.profile) e2.prof = &prof;
     s = e2.setup(sx, h->nev, h->store_cap, bs2);
     if (s == GCGE_OK) {
