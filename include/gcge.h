@@ -215,6 +215,13 @@ int gcge_vc_f32(int64_t n, int d, int q, double alpha, const float *d_V, int64_t
                 const double *d_C, int64_t ldc, double beta, float *d_Y, int64_t ldy,
                 int tc, void *stream);
 
+/* Status of the tensor-core kernels (tc != 0 above, and the solver's FP32 phase):
+ * synchronises `stream`, returns GCGE_ETIMEOUT if a kernel's bounded internal wait
+ * ran out since the last call (that launch's output is invalid; the flag is then
+ * cleared), else GCGE_OK.  Not part of the paper: the asynchronous entry points above
+ * cannot return the status themselves. */
+int gcge_tc_status(void *stream);
+
 /* Dense symmetric eigensolve of STEP 3 (the paper's dsyevx role), FP64 on the
  * device by parallel cyclic Jacobi: d_A (d x d column-major, lda) is
  * overwritten; d_w receives the d eigenvalues ascending, d_Q (ldq) the

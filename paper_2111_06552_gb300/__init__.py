@@ -97,6 +97,7 @@ _SIGS = {
     "gcge_block_cg_f32": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
     "gcge_borth_f64": (_I, [_I64, _P, _P, _P, _P, _I64, _I, _P, _I64, _I, _I, C.POINTER(_I), _P]),
     "gcge_random_block_f64": (_I, [_I64, _I, C.c_uint64, _P, _I64, _P]),
+    "gcge_tc_status": (_I, [_P]),
     "gcge_gram_f64_noalloc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
 }
 GCGE_GRAM_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
@@ -215,6 +216,11 @@ def gcge_borth_f64(n, Brp, Bci, Bval, Q, ldq, q, W, ldw, m, leaf=16, stream=None
                                 _addr(W), ldw, m, leaf, C.byref(out), _stream(stream)),
            "gcge_borth_f64")
     return out.value
+
+
+def gcge_tc_status(stream=None):
+    """GCGE_OK, or raises on GCGE_ETIMEOUT (a tensor-core kernel's bounded wait ran out)."""
+    return _check(lib().gcge_tc_status(_stream(stream)), "gcge_tc_status")
 
 
 def gcge_random_block_f64(n, k, seed, X, ld, stream=None):

@@ -200,6 +200,16 @@ int gcge_borth_f64(int64_t n, const int32_t *Brp, const int32_t *Bci, const doub
                           as_stream(stream));
 }
 
+int gcge_tc_status(void *stream) {
+  int flag = 0;
+  GCGE_CHECK(tc_error_flag(&flag, as_stream(stream)));
+  if (flag) {
+    record_message("a tensor-core kernel's bounded wait ran out; its output is invalid");
+    return GCGE_ETIMEOUT;
+  }
+  return GCGE_OK;
+}
+
 int gcge_random_block_f64(int64_t n, int k, uint64_t seed, double *X, int64_t ld, void *stream) {
   if (n < 0 || k < 0 || ld < k) return GCGE_EINVAL;
   if (n > 0 && k > 0 && bad_ptr(X)) return GCGE_EINVAL;

@@ -377,11 +377,13 @@ template int vc_tc<double>(int64_t, int, int, double, const double *, int64_t, c
                            int64_t, double, double *, int64_t, cudaStream_t, Scratch *);
 
 // Device flag set by a tensor-core kernel whose bounded mbarrier wait timed out.
+// Read and clear it (a set flag is reported once).
 int tc_error_flag(int *host_val, cudaStream_t st) {
   int *err = nullptr;
   GCGE_CHECK(tc::err_flag(&err));
   GCGE_CUDA(cudaMemcpyAsync(host_val, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GCGE_CUDA(cudaStreamSynchronize(st));
+  if (*host_val) GCGE_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
   return GCGE_OK;
 }
 

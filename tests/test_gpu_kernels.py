@@ -290,6 +290,7 @@ def test_gram_f32_tc_layouts(g, n, m, k, offx, offy, ldx, ldy):
     bound = 1.5 * np.abs(X.astype(np.float64)).T @ np.abs(Y.astype(np.float64))
     assert np.all(np.abs(got[:m] - ref) <= 2e-6 * bound + 1e-12)
     assert np.all(got[m:] == 5.0)
+    assert g.gcge_tc_status() == 0   # no bounded wait ran out
 
 
 @pytest.mark.parametrize("n,d,q,offv,offy,ldv,ldy,beta", [
@@ -323,6 +324,7 @@ def test_vc_f32_tc_layouts(g, n, d, q, offv, offy, ldv, ldy, beta):
     mask = np.ones(got.shape, dtype=bool)
     mask[:, offy:offy + q] = False
     assert np.all(np.isnan(got[mask]))
+    assert g.gcge_tc_status() == 0
 
 
 def test_gram_f32_tc_long_rows(g):
