@@ -151,6 +151,25 @@ def test_orth_drops_dependent_columns_and_deflates():
     assert np.abs(Y.T @ BY - np.eye(3)).max() < 1e-13
 
 
+def test_deflation_keeps_small_new_directions():
+    """A correction that differs from span(Q) by 1e-11 (a pair near its tolerance)
+    keeps its new direction -- exactly that direction, B-normalised -- while a
+    column inside span(Q) up to rounding is dropped."""
+    A, B = _pencil_small()
+    rng = np.random.default_rng(11)
+    n = B.shape[0]
+    Q, _ = O.b_orthonormalize(rng.standard_normal((n, 4)), None, B)
+    z = rng.standard_normal(n)
+    z -= Q @ (Q.T @ (B @ z))
+    z /= np.sqrt(z @ (B @ z))                       # B-unit, B-orthogonal to Q
+    w_small = Q[:, 0] + 1e-11 * z                   # new direction of relative size 1e-11
+    w_inside = Q @ rng.standard_normal(4)           # no new direction at all
+    Wd, BWd = O.deflate_against(np.column_stack([w_small, w_inside]), Q, B)
+    assert Wd.shape[1] == 1
+    cos = abs(Wd[:, 0] @ (B @ z)) / np.sqrt(Wd[:, 0] @ BWd[:, 0])
+    assert cos > 1 - 1e-6
+
+
 def test_modified_block_orth_alg2():
     A, B = _pencil_small()
     rng = np.random.default_rng(8)
