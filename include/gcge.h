@@ -132,9 +132,14 @@ int gcge_options_default(gcge_options *opt);
  *   block_size  blockSize (the paper's default is nev/5), 1 <= block_size <= nev.
  *   tol    relative residual ||A x - lambda B x|| / (|lambda| ||B^{1/2} x||) (Section 4).
  *   opt    NULL for defaults.
- *   stream cudaStream_t as void*, used by every later call on this handle.
+ *   stream cudaStream_t as void*, used by this call (device-resident A and B are
+ *          read on it) and by every later call on this handle.
  *   out    receives the handle (NULL on failure).
- * Errors: EINVAL (bad sizes/CSR), ENOMEM, ECUDA. */
+ * The storage checks run on the device after the copy; the call returns when the
+ * copies are complete.
+ * Errors: EINVAL (bad sizes, or a malformed CSR: row_ptr not non-decreasing from 0
+ * to nnz, a column outside [0, n), columns not strictly increasing within a row),
+ * else ENAN (a value that is not finite), ENOMEM, ECUDA. */
 int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, double tol,
                 const gcge_options *opt, void *stream, gcge_handle **out);
 

@@ -18,61 +18,145 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
 
 namespace {
 
-struct HostCsr {
-  int64_t n = 0, nnz = 0;
-  std::vector<int32_t> rp, ci;
-  std::vector<double> val;
-};
+// ---------------------------------------------------------------- matrix intake
+// The caller's CSR arrays go to the device as they are; the checks, the FP32 copy
+// of the values and the union pattern of S = A - theta B are formed there.
 
-int fetch_csr(const gcge_csr *m, HostCsr &out) {
-  out.n = m->n;
-  out.nnz = m->nnz;
-  out.rp.resize(m->n + 1);
-  out.ci.resize(m->nnz);
-  out.val.resize(m->nnz);
-  const cudaMemcpyKind kind = m->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-  GCGE_CUDA(cudaMemcpy(out.rp.data(), m->row_ptr, sizeof(int32_t) * (m->n + 1), kind));
-  if (m->nnz > 0) {
-    GCGE_CUDA(cudaMemcpy(out.ci.data(), m->col_idx, sizeof(int32_t) * m->nnz, kind));
-    GCGE_CUDA(cudaMemcpy(out.val.data(), m->val, sizeof(double) * m->nnz, kind));
-  }
-  return GCGE_OK;
+// Grid for the one-pass intake kernels (rows or entries, grid-stride).
+int intake_grid(int64_t tot) {
+  const int64_t cap = (int64_t)device_sm_count() * 8;
+  int64_t g = (tot + 255) / 256;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
 }
 
-int validate(const HostCsr &m) {
-  if (m.rp[0] != 0 || m.rp[m.n] != m.nnz) return GCGE_EINVAL;
-  for (int64_t i = 0; i < m.n; ++i) {
-    if (m.rp[i + 1] < m.rp[i]) return GCGE_EINVAL;
-    for (int64_t e = m.rp[i]; e < m.rp[i + 1]; ++e) {
-      const int32_t c = m.ci[e];
-      if (c < 0 || c >= m.n) return GCGE_EINVAL;
-      if (e > m.rp[i] && c <= m.ci[e - 1]) return GCGE_EINVAL;   // sorted, no duplicates
-      if (!std::isfinite(m.val[e])) return GCGE_ENAN;
+// Storage checks of one CSR matrix, one thread per row.  flags[0]: malformed
+// pattern (row_ptr not a non-decreasing path from 0 to nnz, a column outside
+// [0, n), columns not strictly increasing in a row); flags[1]: a value that is
+// not finite; *nodiag: some row does not store its diagonal entry.  Every read
+// stays inside row_ptr[0..n] and, for a row whose bounds pass, inside [0, nnz).
+__global__ void inspect_csr_kernel(int64_t n, int64_t nnz, const int32_t *__restrict__ rp,
+                                   const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                   int *flags, int *nodiag) {
+  bool bad = false, nonfin = false, missing = false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) bad = rp[0] != 0 || (int64_t)rp[n] != nnz;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = rp[i], r1 = rp[i + 1];
+    if (r0 < 0 || r1 < r0 || r1 > nnz) {
+      bad = true;
+      continue;
+    }
+    bool diag = false;
+    int64_t prev = -1;
+    for (int64_t e = r0; e < r1; ++e) {
+      const int64_t c = ci[e];
+      if (c < 0 || c >= n || c <= prev) bad = true;
+      prev = c;
+      diag = diag || c == i;
+      if (!isfinite(val[e])) nonfin = true;
+    }
+    missing = missing || !diag;
+  }
+  // every thread of the block reaches this point: warp votes, then one atomic per warp
+  const unsigned m = 0xffffffffu;
+  const bool any_bad = __any_sync(m, bad), any_nf = __any_sync(m, nonfin),
+             any_miss = __any_sync(m, missing);
+  if ((threadIdx.x & 31) == 0) {
+    if (any_bad) atomicOr(&flags[0], 1);
+    if (any_nf) atomicOr(&flags[1], 1);
+    if (any_miss) atomicOr(nodiag, 1);
+  }
+}
+
+// *differ = 1 when the two patterns (same n, same nnz) are not identical.
+__global__ void same_pattern_kernel(int64_t n, int64_t nnz, const int32_t *__restrict__ rpA,
+                                    const int32_t *__restrict__ ciA,
+                                    const int32_t *__restrict__ rpB,
+                                    const int32_t *__restrict__ ciB, int *differ) {
+  bool d = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t u = t0; u <= n; u += stride) d = d || rpA[u] != rpB[u];
+  for (int64_t u = t0; u < nnz; u += stride) d = d || ciA[u] != ciB[u];
+  if (__any_sync(0xffffffffu, d) && (threadIdx.x & 31) == 0) atomicOr(differ, 1);
+}
+
+__global__ void values_to_f32_kernel(int64_t nnz, const double *__restrict__ v,
+                                     float *__restrict__ f) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nnz;
+       u += (int64_t)gridDim.x * blockDim.x)
+    f[u] = (float)v[u];
+}
+
+// Union pattern equal to A's own (B has A's pattern, or B = I and A stores every
+// diagonal entry): entry e of S is entry e of A (and of B).  Runs after the checks
+// passed, so row_ptr is a valid non-decreasing path inside [0, nnz].
+__global__ void identity_maps_kernel(int64_t n, const int32_t *__restrict__ rp,
+                                     const int32_t *__restrict__ ci, int *__restrict__ mapA,
+                                     int *__restrict__ mapB, int *__restrict__ isdiag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      mapA[e] = (int)e;
+      if (mapB) mapB[e] = (int)e;
+      isdiag[e] = ci[e] == i ? 1 : 0;
     }
   }
+}
+
+// Copy the caller's arrays into the handle's device memory (host or device source).
+int upload(const gcge_csr *m, DevCsr &d, cudaStream_t st) {
+  d.n = m->n;
+  d.nnz = m->nnz;
+  const cudaMemcpyKind kind = m->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  GCGE_CUDA(cudaMalloc(&d.rp, sizeof(int32_t) * (m->n + 1)));
+  GCGE_CUDA(cudaMalloc(&d.ci, sizeof(int32_t) * std::max<int64_t>(m->nnz, 1)));
+  GCGE_CUDA(cudaMalloc(&d.v64, sizeof(double) * std::max<int64_t>(m->nnz, 1)));
+  GCGE_CUDA(cudaMemcpyAsync(d.rp, m->row_ptr, sizeof(int32_t) * (m->n + 1), kind, st));
+  GCGE_CUDA(cudaMemcpyAsync(d.ci, m->col_idx, sizeof(int32_t) * m->nnz, kind, st));
+  GCGE_CUDA(cudaMemcpyAsync(d.v64, m->val, sizeof(double) * m->nnz, kind, st));
   return GCGE_OK;
 }
 
-int upload(const HostCsr &m, DevCsr &d, bool want32) {
-  d.n = m.n;
-  d.nnz = m.nnz;
-  GCGE_CUDA(cudaMalloc(&d.rp, sizeof(int32_t) * (m.n + 1)));
-  GCGE_CUDA(cudaMalloc(&d.ci, sizeof(int32_t) * std::max<int64_t>(m.nnz, 1)));
-  GCGE_CUDA(cudaMalloc(&d.v64, sizeof(double) * std::max<int64_t>(m.nnz, 1)));
-  GCGE_CUDA(cudaMemcpy(d.rp, m.rp.data(), sizeof(int32_t) * (m.n + 1), cudaMemcpyHostToDevice));
-  GCGE_CUDA(cudaMemcpy(d.ci, m.ci.data(), sizeof(int32_t) * m.nnz, cudaMemcpyHostToDevice));
-  GCGE_CUDA(cudaMemcpy(d.v64, m.val.data(), sizeof(double) * m.nnz, cudaMemcpyHostToDevice));
-  if (want32) {
-    std::vector<float> f(m.val.begin(), m.val.end());
-    GCGE_CUDA(cudaMalloc(&d.v32, sizeof(float) * std::max<int64_t>(m.nnz, 1)));
-    GCGE_CUDA(cudaMemcpy(d.v32, f.data(), sizeof(float) * m.nnz, cudaMemcpyHostToDevice));
+int make_f32(DevCsr &d, cudaStream_t st) {
+  GCGE_CUDA(cudaMalloc(&d.v32, sizeof(float) * std::max<int64_t>(d.nnz, 1)));
+  values_to_f32_kernel<<<intake_grid(d.nnz), 256, 0, st>>>(d.nnz, d.v64, d.v32);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+
+// Row pointers and columns of a caller's matrix on the host: its own arrays when
+// they are host memory, else a copy.
+struct HostPattern {
+  int64_t n = 0, nnz = 0;
+  const int32_t *rp = nullptr, *ci = nullptr;
+  std::vector<int32_t> rp_copy, ci_copy;
+};
+
+int host_pattern(const gcge_csr *m, HostPattern &p) {
+  p.n = m->n;
+  p.nnz = m->nnz;
+  if (!m->on_device) {
+    p.rp = m->row_ptr;
+    p.ci = m->col_idx;
+    return GCGE_OK;
   }
+  p.rp_copy.resize(m->n + 1);
+  p.ci_copy.resize(m->nnz);
+  GCGE_CUDA(cudaMemcpy(p.rp_copy.data(), m->row_ptr, sizeof(int32_t) * (m->n + 1),
+                       cudaMemcpyDeviceToHost));
+  GCGE_CUDA(cudaMemcpy(p.ci_copy.data(), m->col_idx, sizeof(int32_t) * m->nnz,
+                       cudaMemcpyDeviceToHost));
+  p.rp = p.rp_copy.data();
+  p.ci = p.ci_copy.data();
   return GCGE_OK;
 }
 
-// Union pattern of A and B (or A and the diagonal when B = I) with the position of
-// each union entry in A and in B (-1 when absent), for S = A - theta B.
-int build_union(const HostCsr &A, const HostCsr *B, gcge_handle *h) {
+// General union pattern of A and B (or A and the diagonal when B = I) with the
+// position of each union entry in A and in B (-1 when absent), for S = A - theta B.
+// Used when the union is not A's own pattern.
+int build_union(const HostPattern &A, const HostPattern *B, gcge_handle *h) {
   const int64_t n = A.n;
   std::vector<int32_t> rp(n + 1, 0), ci;
   std::vector<int> mA, mB, dg;
@@ -123,6 +207,81 @@ int build_union(const HostCsr &A, const HostCsr *B, gcge_handle *h) {
     GCGE_CUDA(cudaMalloc(&h->mapB, sizeof(int) * ci.size()));
     GCGE_CUDA(cudaMemcpy(h->mapB, mB.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice));
   }
+  return GCGE_OK;
+}
+
+// The union is A's own pattern: S shares A's row pointers and columns (copied).
+int identity_union(gcge_handle *h, bool withB) {
+  const int64_t n = h->A.n, nnz = h->A.nnz;
+  h->S.n = n;
+  h->S.nnz = nnz;
+  const size_t e = (size_t)std::max<int64_t>(nnz, 1);
+  GCGE_CUDA(cudaMalloc(&h->S.rp, sizeof(int32_t) * (n + 1)));
+  GCGE_CUDA(cudaMalloc(&h->S.ci, sizeof(int32_t) * e));
+  GCGE_CUDA(cudaMalloc(&h->mapA, sizeof(int) * e));
+  GCGE_CUDA(cudaMalloc(&h->isdiag, sizeof(int) * e));
+  if (withB) GCGE_CUDA(cudaMalloc(&h->mapB, sizeof(int) * e));
+  GCGE_CUDA(cudaMemcpyAsync(h->S.rp, h->A.rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice,
+                            h->st));
+  GCGE_CUDA(cudaMemcpyAsync(h->S.ci, h->A.ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice,
+                            h->st));
+  identity_maps_kernel<<<intake_grid(n), 256, 0, h->st>>>(n, h->A.rp, h->A.ci, h->mapA,
+                                                          withB ? h->mapB : nullptr, h->isdiag);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+
+struct DevFlags {
+  int *p = nullptr;
+  ~DevFlags() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Upload, check and prepare A and B: EINVAL for a malformed pattern, else ENAN for
+// a non-finite value.  Returns after the device copies are complete, so the
+// caller may free its arrays.
+int intake(const gcge_csr *A, const gcge_csr *B, bool want32, gcge_handle *h) {
+  GCGE_CHECK(upload(A, h->A, h->st));
+  if (B) GCGE_CHECK(upload(B, h->B, h->st));
+  // flags: 0 malformed, 1 non-finite, 2 A lacks a diagonal entry, 3 (B's, unused),
+  // 4 patterns of A and B differ
+  DevFlags f;
+  GCGE_CUDA(cudaMalloc(&f.p, 8 * sizeof(int)));
+  GCGE_CUDA(cudaMemsetAsync(f.p, 0, 8 * sizeof(int), h->st));
+  inspect_csr_kernel<<<intake_grid(A->n), 256, 0, h->st>>>(A->n, A->nnz, h->A.rp, h->A.ci,
+                                                           h->A.v64, f.p, f.p + 2);
+  GCGE_LAUNCH_CHECK();
+  const bool same_size = B && B->nnz == A->nnz;
+  if (B) {
+    inspect_csr_kernel<<<intake_grid(B->n), 256, 0, h->st>>>(B->n, B->nnz, h->B.rp, h->B.ci,
+                                                             h->B.v64, f.p, f.p + 3);
+    GCGE_LAUNCH_CHECK();
+    if (same_size) {
+      same_pattern_kernel<<<intake_grid(A->nnz + A->n + 1), 256, 0, h->st>>>(
+          A->n, A->nnz, h->A.rp, h->A.ci, h->B.rp, h->B.ci, f.p + 4);
+      GCGE_LAUNCH_CHECK();
+    }
+  }
+  int hf[8];
+  GCGE_CUDA(cudaMemcpyAsync(hf, f.p, sizeof(hf), cudaMemcpyDeviceToHost, h->st));
+  GCGE_CUDA(cudaStreamSynchronize(h->st));
+  if (hf[0]) return GCGE_EINVAL;
+  if (hf[1]) return GCGE_ENAN;
+  if (want32) {
+    GCGE_CHECK(make_f32(h->A, h->st));
+    if (B) GCGE_CHECK(make_f32(h->B, h->st));
+  }
+  const bool own = B ? (same_size && !hf[4]) : !hf[2];
+  if (own) {
+    GCGE_CHECK(identity_union(h, B != nullptr));
+  } else {
+    HostPattern pa, pb;
+    GCGE_CHECK(host_pattern(A, pa));
+    if (B) GCGE_CHECK(host_pattern(B, pb));
+    GCGE_CHECK(build_union(pa, B ? &pb : nullptr, h));
+  }
+  GCGE_CUDA(cudaStreamSynchronize(h->st));
   return GCGE_OK;
 }
 
@@ -215,17 +374,7 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
   }
   h->size_x = sx;
   const bool want32 = h->opt.precision == GCGE_MIXED;
-  int s = GCGE_OK;
-  {
-    HostCsr ha, hb;
-    s = fetch_csr(A, ha);
-    if (s == GCGE_OK) s = validate(ha);
-    if (s == GCGE_OK && B) s = fetch_csr(B, hb);
-    if (s == GCGE_OK && B) s = validate(hb);
-    if (s == GCGE_OK) s = upload(ha, h->A, want32);
-    if (s == GCGE_OK && B) s = upload(hb, h->B, want32);
-    if (s == GCGE_OK) s = build_union(ha, B ? &hb : nullptr, h);
-  }
+  int s = intake(A, B, want32, h);
   if (s != GCGE_OK) {
     free_handle(h);
     delete h;

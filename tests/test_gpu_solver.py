@@ -137,6 +137,35 @@ def test_mixed_precision_reaches_fp64_accuracy(g):
     assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
 
 
+@pytest.mark.parametrize("kind", ["permuted", "diagonal"])
+def test_union_pattern_differs_from_a(g, kind):
+    """S = A - theta B on a union pattern that is not A's own: B = P A P^T (same nnz,
+    other pattern) or a positive diagonal B (fewer entries).  Dense generalized
+    eigensolve of the 144 x 144 pencil as the reference."""
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+    p = W.fd2d(12)
+    rng = np.random.default_rng(5)
+    if kind == "permuted":
+        P = sp.eye(p.n, format="csr")[rng.permutation(p.n)]
+        B = (P @ p.A @ P.T).tocsr()
+        assert B.nnz == p.A.nnz and not np.array_equal(B.indptr, p.A.indptr)
+    else:
+        B = sp.diags(rng.uniform(0.5, 2.0, p.n)).tocsr()
+    B.sort_indices()
+    nev, bs = 8, 4
+    s = g.Solver(p.A, B, nev, bs, 1e-8, seed=2)
+    ev, X = s.solve()
+    status = s.status
+    s.close()
+    X = np.array(X)
+    w = sl.eigh(p.A.toarray(), B.toarray(), eigvals_only=True)[:nev]
+    assert status == 0
+    assert np.abs(ev - w).max() <= 1e-8 * np.abs(w).max()
+    assert L.residual_norms(p.A, B, X, ev).max() < 1e-8
+    assert np.abs(X.T @ (B @ X) - np.eye(nev)).max() < 1e-10
+
+
 def test_not_converged_returns_partial(g):
     p = W.fd2d(16)
     ev, X, st, status = _solve(g, p, 10, 5, seed=0, max_iter=2)
@@ -161,3 +190,18 @@ def test_invalid_inputs_rejected(g):
     with pytest.raises(g.GcgeError) as e:
         g.Solver(nanm, None, 4, 2)
     assert e.value.status == g.GCGE_ENAN
+    # a row pointer beyond nnz in the middle of the array: rejected, nothing read past nnz
+    badp = p.A.copy()
+    ip = badp.indptr.copy()
+    ip[3] = ip[-1] + 100
+    badp.indptr = ip
+    with pytest.raises(g.GcgeError) as e:
+        g.Solver(badp, None, 4, 2)
+    assert e.value.status == g.GCGE_EINVAL
+    # a column index outside [0, n)
+    badc = p.A.copy()
+    badc.indices = badc.indices.copy()
+    badc.indices[-1] = p.n
+    with pytest.raises(g.GcgeError) as e:
+        g.Solver(badc, None, 4, 2)
+    assert e.value.status == g.GCGE_EINVAL
