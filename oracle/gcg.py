@@ -131,10 +131,13 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
         while c < kx and res[c] < tol:
             c += 1
         l_total = store.shape[1] + lw + c
-        move = p.moving and (lw + c) >= 2 * bs and l_total < nev
+        # Section 3.3 moves the window once 2 blockSize new pairs have converged.  It
+        # is also moved when every unlocked vector of X has converged (the paper does
+        # not treat this case): X would otherwise keep no vector to iterate on
+        move = p.moving and l_total < nev and ((lw + c) >= 2 * bs or c == kx)
         history.append(dict(it=it, nconv=min(l_total, nev), d=d, orth_err=orth_err,
                             res_first=float(res[c]) if c < kx else 0.0,
-                            nP=P.shape[1], nW=W.shape[1]))
+                            nP=P.shape[1], nW=W.shape[1], kx=kx, c=c, lw=lw, move=move))
         if move:
             # ---- moving mechanism: all Ritz vectors of Abar, flush the locked ones
             Xall = Va @ Q
@@ -153,6 +156,8 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
         if l_total >= nev:
             converged = True
             break
+        if X.shape[1] - lw == 0:
+            raise RuntimeError("the search window holds no unlocked vector")
         if it >= p.max_iter:
             break
         bs_new = min(bs, nev - l_total, X.shape[1] - lw)

@@ -232,6 +232,21 @@ def test_gcg_moving_matches_plain():
     assert max(h["d"] for h in r2.history) <= 5 * bs
 
 
+@pytest.mark.parametrize("N,nev,bs,seed", [(18, 30, 4, 1), (16, 24, 3, 9), (14, 20, 2, 4)])
+def test_gcg_moving_window_exhaustion(N, nev, bs, seed):
+    """Section 3.3: on these starts every unlocked vector of the window converges
+    before 2 blockSize new pairs are locked.  The window is then moved (P and W fold
+    into X) instead of being left empty, and the run reaches the closed-form spectrum."""
+    p = W.fd2d(N)
+    r = G.gcg(p.A, None, nev, bs, 1e-8, W.initial_block(p.n, 3 * bs, seed), G.Params(moving=True))
+    assert r.converged
+    ex = W.fd2d_eigs(N, nev)
+    assert np.abs(r.evals - ex).max() <= 1e-8 * ex[0]
+    early = [h for h in r.history if h["move"] and h["c"] == h["kx"] and h["lw"] + h["c"] < 2 * bs]
+    assert early, "the case no longer exercises a move on an exhausted window"
+    assert max(h["d"] for h in r.history) <= 5 * bs
+
+
 def test_gcg_shift_reduces_iterations():
     p = W.fd2d(24)
     nev, bs = 30, 3
