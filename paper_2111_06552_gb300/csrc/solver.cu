@@ -798,9 +798,10 @@ int Engine<T>::rayleigh_ritz(bool first, int d) {
 template <typename T>
 int Engine<T>::convergence(const T *X, int *c_out, int *chunk_start, int *chunk_len) {
   const int chunk = (int)std::min<int64_t>(2 * bs_, ldC_);
-  int c = 0, start = 0, m = 0;
+  int c = 0, start = 0, m = 0, held = 0;   // held: first column of the chunk in AXc_
   while (start < kx_) {
     m = std::min(chunk, kx_ - start);
+    held = start;
     GCGE_CHECK(spA(X + start, ldV_, m, AXc_, ldC_));
     if (!bI_) GCGE_CHECK(spB(X + start, ldV_, m, BXc_, ldC_));
     g_launches += 2;
@@ -824,7 +825,7 @@ int Engine<T>::convergence(const T *X, int *c_out, int *chunk_start, int *chunk_
     start += m;
   }
   *c_out = c;
-  *chunk_start = start;
+  *chunk_start = held;
   *chunk_len = m;
   return GCGE_OK;
 }
@@ -979,9 +980,11 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     GCGE_CHECK(convergence(V_[nxt], &c, &cs, &cl));
     // with a reservoir the window is refilled from it; the moving mechanism takes over
     // once it is used up
+    // (Section 3.3 moves after 2 blockSize new locks; the window is also moved when all
+    // of its unlocked vectors converged, which would otherwise leave X empty)
     const bool reservoir_left = res_ && res_next_ < nres_;
-    const bool move = allow_move && !reservoir_left && h_->moving && (lw_ + c) >= 2 * bs_ &&
-                      nlock_ + c < nev_;
+    const bool move = allow_move && !reservoir_left && h_->moving && nlock_ + c < nev_ &&
+                      ((lw_ + c) >= 2 * bs_ || c == kx_);
     if (c > 0) {
       if (nlock_ + c > store_cap_) {
         record_message("locked-vector store overflow");
@@ -1090,6 +1093,15 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     if (nwn > 0) GCGE_CHECK(copyT(nwn, TMP2_, ldW_, V_[nxt] + xoff + kxn + npn, ldV_));
     toc(2);
     if (prof) prof->harvest();
+    if (kxn + npn + nwn == 0) {
+      if (stagnation_limit > 0) {   // FP32 phase: the FP64 phase restarts from the store
+        stagnated = true;
+        kx_ = 0;
+        break;
+      }
+      record_message("the search window holds no vector to iterate on");
+      return GCGE_EBREAKDOWN;
+    }
     cur_ = nxt;
     off_ = xoff;
     kx_ = kxn;

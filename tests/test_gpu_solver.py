@@ -125,6 +125,19 @@ def test_moving_matches_plain(g):
     assert np.abs(ev2 - ref.evals).max() <= 1e-8 * exact[0]
 
 
+@pytest.mark.parametrize("N,nev,bs,seed", [(18, 30, 4, 1), (16, 24, 3, 9), (14, 20, 2, 4)])
+def test_moving_window_exhaustion(g, N, nev, bs, seed):
+    """Starts on which the oracle sees every unlocked window vector converge before
+    2 blockSize new locks (Section 3.3): the window is moved, never left empty."""
+    p = W.fd2d(N)
+    ev, X, st, status = _solve(g, p, nev, bs, seed=seed, moving=1)
+    exact = W.fd2d_eigs(N, nev)
+    assert status == 0
+    assert np.abs(ev - exact).max() <= 1e-8 * exact[0]
+    assert L.residual_norms(p.A, None, X, ev).max() < 1e-8
+    assert st["moves"] >= 1
+
+
 def test_mixed_precision_reaches_fp64_accuracy(g):
     p = W.make_config("fd3d_128", N=14, seed=1)
     nev, bs = 16, 4
