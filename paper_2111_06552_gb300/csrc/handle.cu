@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -299,6 +300,68 @@ void free_handle(gcge_handle *h) {
   h->store = nullptr;
 }
 
+// Two pinned staging buffers and their events, released (after the stream has
+// drained) on every exit path.
+struct Staging {
+  double *buf[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaStream_t st = nullptr;
+  ~Staging() {
+    if (buf[0] || buf[1]) cudaStreamSynchronize(st);
+    for (int b = 0; b < 2; ++b) {
+      if (buf[b]) cudaFreeHost(buf[b]);
+      if (ev[b]) cudaEventDestroy(ev[b]);
+    }
+  }
+};
+
+// Device n x k (leading dimension n) to host (leading dimension ldv) in pieces of
+// at most 8 MB through two pinned buffers: the GPU fills one while the CPU copies
+// the other into the destination.  The CPU thus writes the caller's pages itself;
+// a direct copy into pageable memory that was never touched runs about a hundred
+// times slower than into touched pages.
+int copy_out_staged(double *dst, int64_t ldv, const double *src, int64_t n, int k,
+                    cudaStream_t st) {
+  int64_t rows = n, cols = k;
+  if (ldv == n) {            // contiguous destination: one flat array
+    rows = n * k;
+    cols = 1;
+  }
+  const int64_t piece = std::min<int64_t>(rows, (int64_t)1 << 20);   // doubles
+  Staging sg;
+  sg.st = st;
+  for (int b = 0; b < 2; ++b) {
+    GCGE_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&sg.buf[b]), sizeof(double) * piece,
+                            cudaHostAllocDefault));
+    GCGE_CUDA(cudaEventCreateWithFlags(&sg.ev[b], cudaEventDisableTiming));
+  }
+  int64_t pc = 0, pr = 0, plen = 0;    // the piece in flight before this one
+  int64_t p = 0;
+  for (int64_t c = 0; c < cols; ++c) {
+    for (int64_t r0 = 0; r0 < rows; r0 += piece) {
+      const int64_t len = std::min(piece, rows - r0);
+      const int b = (int)(p & 1);
+      GCGE_CUDA(cudaMemcpyAsync(sg.buf[b], src + c * n + r0, sizeof(double) * len,
+                                cudaMemcpyDeviceToHost, st));
+      GCGE_CUDA(cudaEventRecord(sg.ev[b], st));
+      if (p > 0) {
+        GCGE_CUDA(cudaEventSynchronize(sg.ev[b ^ 1]));
+        std::memcpy(dst + pc * ldv + pr, sg.buf[b ^ 1], sizeof(double) * plen);
+      }
+      pc = c;
+      pr = r0;
+      plen = len;
+      ++p;
+    }
+  }
+  if (p > 0) {
+    const int b = (int)((p - 1) & 1);
+    GCGE_CUDA(cudaEventSynchronize(sg.ev[b]));
+    std::memcpy(dst + pc * ldv + pr, sg.buf[b], sizeof(double) * plen);
+  }
+  return GCGE_OK;
+}
+
 __global__ void transpose_out_kernel(int64_t n, int k, const int *__restrict__ perm,
                                      const double *__restrict__ S, int64_t lds,
                                      double *__restrict__ out, int64_t ldo) {
@@ -452,11 +515,15 @@ int gcge_eigenpairs(gcge_handle *h, double *evals, double *evecs, int64_t ldv, i
     if (g > 4096) g = 4096;
     transpose_out_kernel<<<(int)g, 256, 0, h->st>>>(h->n, k, dperm, h->store, h->ld_store, dst, ldo);
     GCGE_LAUNCH_CHECK();
-    if (!evecs_on_device) {
-      GCGE_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * ldv, tmp, sizeof(double) * h->n,
-                                  sizeof(double) * h->n, k, cudaMemcpyDeviceToHost, h->st));
-    }
     GCGE_CUDA(cudaStreamSynchronize(h->st));
+    if (!evecs_on_device) {
+      const int s = copy_out_staged(evecs, ldv, tmp, h->n, k, h->st);
+      if (s != GCGE_OK) {
+        cudaFree(dperm);
+        cudaFree(tmp);
+        return s;
+      }
+    }
     cudaFree(dperm);
     if (tmp) cudaFree(tmp);
   }

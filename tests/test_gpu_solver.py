@@ -179,6 +179,34 @@ def test_union_pattern_differs_from_a(g, kind):
     assert np.abs(X.T @ (B @ X) - np.eye(nev)).max() < 1e-10
 
 
+def test_eigenpairs_leading_dimensions(g):
+    """gcge_eigenpairs into host memory with ldv > n (column by column through the
+    staging buffers; padding rows untouched) and into device memory: both equal the
+    contiguous host copy."""
+    import ctypes as C
+    import torch
+    p = W.fd2d(16)
+    nev, bs, n = 12, 4, p.n
+    s = g.Solver(p.A, None, nev, bs, 1e-8, seed=4)
+    ev, X = s.solve()
+    X = np.array(X)
+    ldv = n + 3
+    out = np.full((nev, ldv), -7.0)
+    ev2 = np.zeros(nev)
+    nc = C.c_int(0)
+    assert g.lib().gcge_eigenpairs(s.h, ev2.ctypes.data, out.ctypes.data, ldv, 0, C.byref(nc)) == 0
+    assert np.array_equal(ev2, ev)
+    assert np.array_equal(out[:, :n].T, X)
+    assert np.all(out[:, n:] == -7.0)
+    d = torch.full((nev, ldv), -7.0, dtype=torch.float64, device="cuda")
+    assert g.lib().gcge_eigenpairs(s.h, ev2.ctypes.data, d.data_ptr(), ldv, 1, C.byref(nc)) == 0
+    torch.cuda.synchronize()
+    dh = d.cpu().numpy()
+    assert np.array_equal(dh[:, :n].T, X)
+    assert np.all(dh[:, n:] == -7.0)
+    s.close()
+
+
 def test_not_converged_returns_partial(g):
     p = W.fd2d(16)
     ev, X, st, status = _solve(g, p, 10, 5, seed=0, max_iter=2)
