@@ -18,9 +18,10 @@
 //
 // Optional fused epilogue (used by the CG step): per column j the dot product
 // sum_i X[i, j] (A X)[i, j].  Lanes holding the same columns reduce over the rows of
-// the warp with shuffles, then over the CTA in shared memory; every CTA writes one
-// partial row and the last CTA to finish (atomic ticket) sums the partials in a
-// fixed order into dot_out[0:k], so the result is deterministic.
+// the warp with shuffles, then over the CTA with shared-memory atomic adds; every CTA
+// writes one partial row and the last CTA to finish (atomic ticket) sums the
+// partials in a fixed order into dot_out[0:k].  The order of the warps' atomic adds
+// is not fixed, so two runs can differ in the last bits of the dot products.
 #include "spmm.cuh"
 
 namespace gcge {
