@@ -3,7 +3,7 @@
 // All k columns advance together with per-column scalars, which equals k
 // independent CG runs.  One CG step is three kernels:
 //   1. q = S p, with the per-column dots p^T q fused into the SpMM epilogue
-//      (finished deterministically by the last CTA into pq[k]);
+//      (summed across CTAs in a fixed order by the last CTA into pq[k]);
 //   2. alpha_j = rr_j / pq_j; x += alpha p, r -= alpha q; per-column r^T r
 //      (last CTA: rr_new[k], and the breakdown flags for p^T S p <= 0);
 //   3. beta_j = rr_new_j / rr_j; p = r + beta p (last CTA commits rr, the step
