@@ -1077,7 +1077,8 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     if (res_ && res_next_ < nres_ && kxn < sizeX_) {
       rres = std::min(nres_ - res_next_, sizeX_ - kxn);
       rres = std::min(rres, (int)ldW_ - bsn);
-      rres = std::min(rres, dmax_ - (kxn + npn + bsn));
+      // the next basis [X_a, P, W] starts at column xoff of V[nxt] and must end by dmax_
+      rres = std::min(rres, dmax_ - (xoff + kxn + npn + bsn));
       rres = std::max(rres, 0);
       if (rres > 0) {
         g_launches += 1;
