@@ -331,8 +331,16 @@ int copy_out_staged(double *dst, int64_t ldv, const double *src, int64_t n, int 
   Staging sg;
   sg.st = st;
   for (int b = 0; b < 2; ++b) {
-    GCGE_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&sg.buf[b]), sizeof(double) * piece,
-                            cudaHostAllocDefault));
+    if (cudaHostAlloc(reinterpret_cast<void **>(&sg.buf[b]), sizeof(double) * piece,
+                      cudaHostAllocDefault) != cudaSuccess) {
+      // no pinned memory to stage through: one direct copy
+      (void)cudaGetLastError();
+      sg.buf[b] = nullptr;
+      GCGE_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * ldv, src, sizeof(double) * n,
+                                  sizeof(double) * n, k, cudaMemcpyDeviceToHost, st));
+      GCGE_CUDA(cudaStreamSynchronize(st));
+      return GCGE_OK;
+    }
     GCGE_CUDA(cudaEventCreateWithFlags(&sg.ev[b], cudaEventDisableTiming));
   }
   int64_t pc = 0, pr = 0, plen = 0;    // the piece in flight before this one
