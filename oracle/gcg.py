@@ -57,6 +57,9 @@ class Params:
     moving: bool = False
     size_x: int | None = None
     orth: OrthParams = field(default_factory=OrthParams)
+    # optional observer called with a dict at STEP 5 and STEP 6 (tests read the
+    # iteration's intermediate blocks through it; it never changes the iteration)
+    trace: object = None
 
 
 @dataclass
@@ -67,6 +70,14 @@ class Result:
     iterations: int
     converged: bool
     history: list
+
+
+def p_tilde(xh: np.ndarray, c: int, bs_new: int, nb_old: int) -> np.ndarray:
+    """Eq. CP_tilde: the Ritz coefficients of the next active block with the rows of
+    the old active block X_n zeroed (its rows come first in V_a = [X_a, P, W])."""
+    pt = np.array(xh[:, c:c + bs_new], copy=True)
+    pt[:nb_old, :] = 0.0
+    return pt
 
 
 def _l2_orthonormal_against(pt: np.ndarray, xh: np.ndarray, drop: float) -> np.ndarray:
@@ -167,14 +178,16 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
                 P = np.zeros((n, 0))
             else:
                 xh = Q[:, :kx]
-                pt = np.array(xh[:, c:c + bs_new], copy=True)
-                pt[:nb_old, :] = 0.0
-                ph = _l2_orthonormal_against(pt, xh, p.p_drop)
+                ph = _l2_orthonormal_against(p_tilde(xh, c, bs_new, nb_old), xh, p.p_drop)
                 P = Va @ ph
+                if p.trace is not None:
+                    p.trace(dict(step=5, it=it, Xnew=Xa_new, c=c, bs_new=bs_new, P=P))
         # ---- STEP 6: shifted CG from the active block
         locked_lam = np.concatenate([store_lam, lam[:lw]])
         theta = float(np.max(locked_lam)) if (p.use_shift and locked_lam.size) else 0.0
         Xn = X[:, lw:lw + bs_new]
+        if p.trace is not None:
+            p.trace(dict(step=6, it=it, Xn=Xn))
         Wt, cg_it, _ = shifted_cg(A, B, theta, Xn, lam[lw:lw + bs_new], p.cg_max_iter, p.cg_rtol)
         history[-1].update(theta=theta, cg_iters=int(cg_it.max()) if cg_it.size else 0)
         # ---- STEP 2: B-orthogonalise W against [X_c (store), X, P], then Algorithm 3

@@ -1091,6 +1091,10 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     int nwn = 0;
     GCGE_CHECK(borth(TMP2_, bsn + rres, parts, 2, &nwn));
     kgrow_ = rres;
+    if (xoff + kxn + npn + nwn > dmax_) {   // the next basis must fit the row width of V
+      record_message("basis [X_a, P, W] wider than the basis buffer");
+      return GCGE_EINVAL;
+    }
     if (nwn > 0) GCGE_CHECK(copyT(nwn, TMP2_, ldW_, V_[nxt] + xoff + kxn + npn, ldV_));
     toc(2);
     if (prof) prof->harvest();

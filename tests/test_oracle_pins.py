@@ -361,10 +361,9 @@ def test_planted_orth_missing_deflation_is_caught(monkeypatch):
         test_orth_drops_dependent_columns_and_deflates()
 
 
-def test_planted_transposed_p_rows_is_caught(monkeypatch):
-    # zeroing the wrong rows of p~ (the paper's Eq. CP_tilde) leaves P coupled to X
-    orig = G._l2_orthonormal_against
-
+def test_planted_missing_p_projection_is_caught(monkeypatch):
+    # without the L2 orthogonalisation of p~ against x^ (Eq. Equality_Cpx) P stays
+    # coupled to X and the basis V_a loses its B-orthonormality
     def skip_projection(pt, xh, drop):
         lam, Q = L.sym_eig(pt.T @ pt)
         keep = lam > drop * drop
@@ -374,3 +373,85 @@ def test_planted_transposed_p_rows_is_caught(monkeypatch):
     p = W.q1_kron(6)
     r = G.gcg(p.A, p.B, 8, 2, 1e-8, W.initial_block(p.n, 14, 0), G.Params(max_iter=6))
     assert max(h["orth_err"] for h in r.history) > 1e-6
+
+
+# ---------------------------------------------------------------- STEP 5 (P)
+def _b_basis(Y, B):
+    """A B-orthonormal basis of span(Y) (test-side, dense)."""
+    BY = Y if B is None else B @ Y
+    lam, Q = np.linalg.eigh(Y.T @ BY)
+    keep = lam > 1e-20 * max(lam.max(), 1e-300)
+    return Y @ (Q[:, keep] / np.sqrt(lam[keep]))
+
+
+def _step5_pin(pencil, nev, bs, seed, max_iter, moving=False):
+    """P^new of the oracle against the paper's own definition before Eq. CP_tilde:
+    P~ = V x^_n - X_n (X_n^T B V x^_n), with X_n the block that produced W (recorded
+    at STEP 6 of the previous iteration) and V x^_n the new Ritz vectors of the next
+    active block; P^new must span P~ B-orthogonalised against X^new, and satisfy
+    (X^new)^T B P^new = O, (P^new)^T B P^new = I (the identities after Eq. Equality_Cpx)."""
+    events = []
+    size_x = 3 * bs if moving else nev + 3 * bs
+    X0 = W.initial_block(pencil.n, size_x, seed)
+    G.gcg(pencil.A, pencil.B, nev, bs, 1e-8, X0,
+          G.Params(max_iter=max_iter, moving=moving, trace=events.append))
+    B = pencil.B
+    Bm = (lambda Y: Y) if B is None else (lambda Y: B @ Y)
+    checked = 0
+    xn_prev = None
+    for e in events:
+        if e["step"] == 6:
+            xn_prev = e["Xn"]
+            continue
+        Xnew, c, b, P = e["Xnew"], e["c"], e["bs_new"], e["P"]
+        Vxn = Xnew[:, c:c + b]
+        Pt = Vxn - xn_prev @ (xn_prev.T @ Bm(Vxn))
+        for _ in range(2):
+            Pt = Pt - Xnew @ (Bm(Xnew).T @ Pt)
+        # P~ is a difference of nearly equal blocks once X_n has nearly converged; its
+        # direction is then fixed only to eps / sigma_min(P~), so such steps are skipped
+        if np.linalg.eigvalsh(Pt.T @ Bm(Pt)).min() < 1e-12:
+            continue
+        Qt = _b_basis(Pt, B)
+        BP = Bm(P)
+        assert P.shape[1] == Qt.shape[1] == b
+        assert np.abs(P.T @ BP - np.eye(b)).max() < 1e-10
+        assert np.abs(Xnew.T @ BP).max() < 1e-10
+        # span(P^new) = span(P~ projected): the part of P outside span(Qt) vanishes
+        outside = P - Qt @ (Qt.T @ BP)
+        assert np.sqrt(np.einsum("ij,ij->j", outside, Bm(outside))).max() < 1e-8
+        checked += 1
+    assert checked >= 3
+    return checked
+
+
+@pytest.mark.parametrize("name,moving", [("q1var", False), ("fd2d", False), ("fd2d", True)])
+def test_step5_p_spans_paper_definition(name, moving):
+    if name == "q1var":
+        p = W.q1_var(6, W.lognormal_cells((7, 7, 7), 1.0, 3))
+        _step5_pin(p, 8, 2, 0, 8)
+    else:
+        p = W.fd2d(12)
+        _step5_pin(p, 12, 2, 1, 12, moving=moving)
+
+
+def test_planted_wrong_p_rows_is_caught(monkeypatch):
+    # Eq. CP_tilde zeroes the rows of the old active block X_n; zeroing the next
+    # nb_old rows (those of X_n~) instead must fail the STEP 5 pin
+    def wrong_rows(xh, c, bs_new, nb_old):
+        pt = np.array(xh[:, c:c + bs_new], copy=True)
+        pt[nb_old:2 * nb_old, :] = 0.0
+        return pt
+
+    monkeypatch.setattr(G, "p_tilde", wrong_rows)
+    p = W.q1_var(6, W.lognormal_cells((7, 7, 7), 1.0, 3))
+    with pytest.raises(AssertionError):
+        _step5_pin(p, 8, 2, 0, 8)
+
+
+def test_planted_no_p_is_caught(monkeypatch):
+    # P never formed (p~ empty): the pin sees a P of the wrong width
+    monkeypatch.setattr(G, "p_tilde", lambda xh, c, bs_new, nb_old: xh[:, :0].copy())
+    p = W.q1_var(6, W.lognormal_cells((7, 7, 7), 1.0, 3))
+    with pytest.raises(AssertionError):
+        _step5_pin(p, 8, 2, 0, 8)
