@@ -44,7 +44,7 @@ import numpy as np
 
 from .linalg import spmm, b_norms, sym_eig, residual_norms
 from .cg import shifted_cg
-from .orth import OrthParams, b_orthonormalize
+from .orth import OrthParams, b_orthonormalize, b_orthonormalize_alg2
 
 
 @dataclass
@@ -57,6 +57,7 @@ class Params:
     moving: bool = False
     size_x: int | None = None
     orth: OrthParams = field(default_factory=OrthParams)
+    orth_alg: int = 3            # STEP 2 by Algorithm 3 (default) or Algorithm 2
     # optional observer called with a dict at STEP 5 and STEP 6 (tests read the
     # iteration's intermediate blocks through it; it never changes the iteration)
     trace: object = None
@@ -109,8 +110,9 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
     if X0.shape != (n, size_x):
         raise ValueError(f"X0 must be {n} x {size_x}")
 
-    # ---- STEP 1/2: orthonormalise the initial block (Algorithm 3)
-    X, _ = b_orthonormalize(np.array(X0, dtype=np.float64), None, B, p.orth)
+    borth = b_orthonormalize if p.orth_alg == 3 else b_orthonormalize_alg2
+    # ---- STEP 1/2: orthonormalise the initial block (Algorithm 3, or Algorithm 2)
+    X, _ = borth(np.array(X0, dtype=np.float64), None, B, p.orth)
     if X.shape[1] != size_x:
         raise ValueError("initial block is rank deficient")
     lam = np.zeros(size_x)
@@ -192,7 +194,7 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
         history[-1].update(theta=theta, cg_iters=int(cg_it.max()) if cg_it.size else 0)
         # ---- STEP 2: B-orthogonalise W against [X_c (store), X, P], then Algorithm 3
         Q0 = np.hstack([store, X, P])
-        W, _ = b_orthonormalize(Wt, Q0, B, p.orth)
+        W, _ = borth(Wt, Q0, B, p.orth)
         nb_old = bs_new
 
     allX = np.hstack([store, X[:, :lw]])

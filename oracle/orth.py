@@ -131,15 +131,44 @@ def b_orthonormalize(W: np.ndarray, Q: np.ndarray | None, B, p: OrthParams = Ort
     return recursive_orth_svd(W, BW, p)
 
 
+def _mgs_block(X: np.ndarray, BX: np.ndarray, p: OrthParams):
+    """Modified Gram-Schmidt inside one block in the B inner product (Algorithm 2's
+    per-block step): column j is scaled to unit B-norm and removed from every later
+    column of the block at once.  A column whose B-norm has fallen to ``drop_tol``
+    (the columns start Algorithm 2 at unit B-norm) is linearly dependent: it is
+    removed and the block's rearmost column takes its place (Section 3.1).  The pass
+    is repeated while the block's Gram differs from I by more than ``leaf_tol`` (at
+    most ``leaf_max`` passes), as the "small enough" loops of Algorithm 2 are."""
+    X, BX = X.copy(), BX.copy()
+    for _ in range(p.leaf_max):
+        m = X.shape[1]
+        j = 0
+        while j < m:
+            s = float(np.sqrt(max(X[:, j] @ BX[:, j], 0.0)))
+            if s <= p.drop_tol:
+                X[:, j], BX[:, j] = X[:, m - 1], BX[:, m - 1]
+                m -= 1
+                continue
+            X[:, j] /= s
+            BX[:, j] /= s
+            r = X[:, j + 1:m].T @ BX[:, j]
+            X[:, j + 1:m] -= np.outer(X[:, j], r)
+            BX[:, j + 1:m] -= np.outer(BX[:, j], r)
+            j += 1
+        X, BX = X[:, :m], BX[:, :m]
+        if m == 0 or float(np.max(np.abs(X.T @ BX - np.eye(m)))) <= p.leaf_tol:
+            break
+    return X, BX
+
+
 def modified_block_orth(X: np.ndarray, X0: np.ndarray | None, B, b: int | None = None,
                         p: OrthParams = OrthParams()):
     """Algorithm 2 (modified block orthogonalisation), block size b = min(m/4, 200).
 
     Deflation against X0 as in ``deflate_against``; then for k = 1..l: the block
-    X_k is orthonormalised (the leaf step of Algorithm 3 stands in for the
-    modified Gram-Schmidt of one block), and all later blocks together are
-    deflated against it, R = [X_{k+1},...,X_l]^T (B X_k), repeated until R is
-    small.
+    X_k is orthonormalised by modified Gram-Schmidt (``_mgs_block``), and all later
+    blocks together are deflated against it, R = [X_{k+1},...,X_l]^T (B X_k),
+    X_rest -= X_k R^T, repeated until R is small relative to the columns.
     """
     X, BX = deflate_against(X, X0, B, p)
     m = X.shape[1]
@@ -148,7 +177,7 @@ def modified_block_orth(X: np.ndarray, X0: np.ndarray | None, B, b: int | None =
     done, Bdone = [], []
     rest, Brest = X, BX
     while rest.shape[1] > 0:
-        Xk, BXk = _leaf(rest[:, :b], Brest[:, :b], p)
+        Xk, BXk = _mgs_block(rest[:, :b], Brest[:, :b], p)
         done.append(Xk)
         Bdone.append(BXk)
         rest, Brest = rest[:, b:], Brest[:, b:]
@@ -163,3 +192,8 @@ def modified_block_orth(X: np.ndarray, X0: np.ndarray | None, B, b: int | None =
             if crit <= p.inner_tol:
                 break
     return np.hstack(done), np.hstack(Bdone)
+
+
+def b_orthonormalize_alg2(W: np.ndarray, Q: np.ndarray | None, B, p: OrthParams = OrthParams()):
+    """STEP 2 with Algorithm 2 in place of Algorithm 3 (the paper's alternative)."""
+    return modified_block_orth(W, Q, B, None, p)

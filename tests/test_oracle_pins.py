@@ -180,6 +180,55 @@ def test_modified_block_orth_alg2():
     assert np.abs(Y @ (BY.T @ X) - X).max() < 1e-11 * np.abs(X).max()
 
 
+@pytest.mark.parametrize("withB", [False, True])
+def test_alg2_equals_cholesky_qr(withB):
+    """Block modified Gram-Schmidt takes each column against all earlier ones in
+    order, so without drops it gives the B-QR factor X R^-1 with R the Cholesky factor
+    of X^T B X (positive diagonal) -- a textbook routine, whatever the block size."""
+    A, B = _pencil_small()
+    B = B if withB else None
+    rng = np.random.default_rng(11)
+    n = A.shape[0]
+    X = rng.standard_normal((n, 20)) @ np.diag(np.logspace(0, -3, 20))
+    BX = X if B is None else B @ X
+    s = np.sqrt(np.einsum("ij,ij->j", X, BX))
+    Xs = X / s                           # Algorithm 2 starts from unit B-norm columns
+    R = np.linalg.cholesky(Xs.T @ (Xs if B is None else B @ Xs)).T
+    Yref = np.linalg.solve(R.T, Xs.T).T
+    for b in (1, 5, 7, 20):
+        Y, BY = O.modified_block_orth(X, None, B, b)
+        assert Y.shape[1] == 20
+        assert np.abs(Y - Yref).max() < 1e-9 * np.abs(Yref).max()
+
+
+def test_alg2_drops_dependent_columns():
+    A, B = _pencil_small()
+    rng = np.random.default_rng(12)
+    n = A.shape[0]
+    Q, _ = O.b_orthonormalize(rng.standard_normal((n, 4)), None, B)
+    X = rng.standard_normal((n, 12))
+    X[:, 5] = X[:, 1] + X[:, 2]                # inside the block's own span
+    X[:, 9] = Q @ rng.standard_normal(4)       # inside span(Q)
+    Y, BY = O.modified_block_orth(X, Q, B, 3)
+    assert Y.shape[1] == 10
+    assert np.abs(Y.T @ BY - np.eye(10)).max() < 1e-12
+    assert np.abs(Q.T @ BY).max() < 1e-12
+    # span(Y) + span(Q) holds every input column
+    QY = np.hstack([Q, Y])
+    res = X - QY @ (np.hstack([B @ Q, BY]).T @ X)
+    assert np.abs(res).max() < 1e-10 * np.abs(X).max()
+
+
+def test_gcg_with_alg2_closed_form():
+    p = W.fd2d(16)
+    nev, bs = 12, 3
+    r = G.gcg(p.A, None, nev, bs, 1e-8, W.initial_block(p.n, nev + 3 * bs, 2),
+              G.Params(orth_alg=2))
+    exact = W.fd2d_eigs(16, nev)
+    assert r.converged
+    assert np.abs(r.evals - exact).max() <= 1e-8 * exact[0]
+
+
 # ---------------------------------------------------------------- full GCG (Algorithm 1)
 def test_gcg_fd2d_closed_form():
     p = W.fd2d(20)
