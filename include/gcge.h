@@ -75,7 +75,7 @@ typedef struct {
   int use_shift;            /* dynamic shift theta of Section 3.2                     (1)   */
   int orth_leaf;            /* Algorithm 3 leaf width c = min(m, orth_leaf)          (16)  */
   int moving;               /* 1: moving mechanism of Section 3.3, 0: off, -1: auto (-1)  */
-  int size_x;               /* 0: min(nev + 3 bs, n) (3 bs when moving)               (0)   */
+  int size_x;               /* 0: min(nev + 3 bs, n) (moving: max_proj_dim - 2 bs)   (0)   */
   int max_iter;             /* GCG iterations (Rayleigh-Ritz solves) before ENOTCONV (2000) */
   uint64_t seed;            /* initial block N(0,1) from splitmix64 + Box-Muller      (0)   */
   const double *initial_block; /* optional host n x size_x row-major start block (NULL) */
@@ -85,7 +85,18 @@ typedef struct {
                                matrix with an explicit V^T A V and V^T B V with I (slow) */
   int profile;              /* 1: time every kernel class with CUDA events           (0)   */
   int mixed_bs2;            /* MIXED: active block width of the FP64 phase; 0: blockSize (0) */
+  int orth;                 /* STEP 2 orthogonaliser: GCGE_ORTH_ALG3 (RecursiveOrthSVD,
+                               Algorithm 3) or GCGE_ORTH_ALG2 (modified block
+                               orthogonalisation, Algorithm 2), Section 3.1        (ALG3) */
+  int max_proj_dim;         /* moving mechanism (Section 3.3): largest dimension of the
+                               projection subspace [X, P, W]; the X window is then
+                               max_proj_dim - 2 blockSize columns. 0: 5 blockSize.
+                               Must be >= 3 blockSize; ignored without moving.   (0)   */
 } gcge_options;
+
+#define GCGE_ORTH_ALG3 0      /* Algorithm 3: recursive halves, leaf M = W^T B W eigensolve */
+#define GCGE_ORTH_ALG2 1      /* Algorithm 2: blocks of b = min(m/4, 200) columns, modified
+                                 Gram-Schmidt inside a block, block deflation of the rest */
 
 /* Kernel classes of the per-kernel profile in gcge_stats (profile = 1). */
 #define GCGE_K_SPMM 0         /* FP32 CSR x block products (SpMM), incl. the CG SpMM + dot */
@@ -118,6 +129,8 @@ typedef struct {
   int64_t prof_calls[12];
   double prof_bytes[12];
   double prof_flops[12];
+  int refills;              /* MIXED + moving: phase-1 vectors that refilled the FP64
+                               phase's window beside W                                */
 } gcge_stats;
 
 /* ----------------------------------------------------------------- solver */
@@ -249,15 +262,16 @@ int gcge_block_cg_f32(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col_
                       const float *d_S, int k, const float *d_B, int64_t ldb, float *d_X,
                       int64_t ldx, int max_iter, double rtol, int *iters, void *stream);
 
-/* STEP 2: B-orthonormalise the n x m block d_W (row-major, ldw, overwritten)
- * against the B-orthonormal block d_Q (n x q, ldq; q may be 0) and by
- * Algorithm 3 with leaf width min(m, leaf).  B is CSR on the device or all
- * three pointers NULL for B = I.  m_out (host) receives the number of columns
- * kept (dependent ones are removed and the rest compacted to the left).
- * Synchronises the stream. */
+/* STEP 2 (Section 3.1): B-orthonormalise the n x m block d_W (row-major, ldw,
+ * overwritten) against the B-orthonormal block d_Q (n x q, ldq; q may be 0), then
+ * by Algorithm 3 with leaf width min(m, leaf) (orth = GCGE_ORTH_ALG3) or by
+ * Algorithm 2, modified block orthogonalisation with blocks of min(m/4, 200)
+ * columns (orth = GCGE_ORTH_ALG2).  B is CSR on the device or all three pointers
+ * NULL for B = I.  m_out (host) receives the number of columns kept (dependent
+ * ones are removed and the rest compacted to the left).  Synchronises the stream. */
 int gcge_borth_f64(int64_t n, const int32_t *d_Brp, const int32_t *d_Bci, const double *d_Bval,
                    const double *d_Q, int64_t ldq, int q, double *d_W, int64_t ldw, int m,
-                   int leaf, int *m_out, void *stream);
+                   int leaf, int orth, int *m_out, void *stream);
 
 /* Gram product without any device allocation (the paper has no counterpart; it
  * exists for callers that cannot allocate while they run -- e.g. their own allocator

@@ -34,6 +34,8 @@ GCGE_ENAN = -7
 GCGE_ENOTREADY = -8
 GCGE_FP64 = 0
 GCGE_MIXED = 1
+GCGE_ORTH_ALG3 = 0
+GCGE_ORTH_ALG2 = 1
 KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other", "spmm64", "gram64", "vc64")
 
 
@@ -56,7 +58,7 @@ class gcge_options(C.Structure):
                 ("size_x", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("initial_block", C.c_void_p), ("mixed_switch_tol", C.c_double),
                 ("verbose", C.c_int), ("checks", C.c_int), ("profile", C.c_int),
-                ("mixed_bs2", C.c_int)]
+                ("mixed_bs2", C.c_int), ("orth", C.c_int), ("max_proj_dim", C.c_int)]
 
 
 class gcge_stats(C.Structure):
@@ -66,7 +68,7 @@ class gcge_stats(C.Structure):
                 ("max_orth_err", C.c_double), ("max_abar_err", C.c_double),
                 ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 12),
                 ("prof_calls", C.c_int64 * 12), ("prof_bytes", C.c_double * 12),
-                ("prof_flops", C.c_double * 12)]
+                ("prof_flops", C.c_double * 12), ("refills", C.c_int)]
 
 
 _P = C.c_void_p
@@ -95,7 +97,8 @@ _SIGS = {
     "gcge_syev": (_I, [_I, _P, _I64, _P, _P, _I64, C.POINTER(_I), _P]),
     "gcge_block_cg_f64": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
     "gcge_block_cg_f32": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
-    "gcge_borth_f64": (_I, [_I64, _P, _P, _P, _P, _I64, _I, _P, _I64, _I, _I, C.POINTER(_I), _P]),
+    "gcge_borth_f64": (_I, [_I64, _P, _P, _P, _P, _I64, _I, _P, _I64, _I, _I, _I, C.POINTER(_I),
+                            _P]),
     "gcge_random_block_f64": (_I, [_I64, _I, C.c_uint64, _P, _I64, _P]),
     "gcge_tc_status": (_I, [_P]),
     "gcge_gram_f64_noalloc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
@@ -210,10 +213,11 @@ def gcge_block_cg_f32(n, row_ptr, col_idx, S, k, Bm, ldb, X, ldx, max_iter, rtol
     return it
 
 
-def gcge_borth_f64(n, Brp, Bci, Bval, Q, ldq, q, W, ldw, m, leaf=16, stream=None):
+def gcge_borth_f64(n, Brp, Bci, Bval, Q, ldq, q, W, ldw, m, leaf=16, orth=GCGE_ORTH_ALG3,
+                   stream=None):
     out = C.c_int(0)
     _check(lib().gcge_borth_f64(n, _addr(Brp), _addr(Bci), _addr(Bval), _addr(Q), ldq, q,
-                                _addr(W), ldw, m, leaf, C.byref(out), _stream(stream)),
+                                _addr(W), ldw, m, leaf, orth, C.byref(out), _stream(stream)),
            "gcge_borth_f64")
     return out.value
 
@@ -299,6 +303,7 @@ def gcge_destroy(h):
 def stats_dict(st: gcge_stats) -> dict:
     return {"iterations": st.iterations, "iterations_fp32": st.iterations_fp32,
             "nconv": st.nconv, "cg_steps": st.cg_steps, "moves": st.moves,
+            "refills": st.refills,
             "ms_total": st.ms_total, "ms_step": list(st.ms_step), "ms_syev": st.ms_syev,
             "max_orth_err": st.max_orth_err, "max_abar_err": st.max_abar_err,
             "kernel_launches": st.kernel_launches,

@@ -101,6 +101,10 @@ int gcge_gram_f64(int64_t n, int m, int k, double alpha, const double *X, int64_
   if (n < 0 || m < 0 || k < 0 || ldx < m || ldy < k || ldc < m) return GCGE_EINVAL;
   if (m == 0 || k == 0) return GCGE_OK;
   if (bad_ptr(C) || (n > 0 && (bad_ptr(X) || bad_ptr(Y)))) return GCGE_EINVAL;
+  if (!gram_f64_grid_ok(m, k)) {
+    record_message("gcge_gram_f64: k needs more than 65535 column tiles");
+    return GCGE_EINVAL;
+  }
   Scratch ws;
   cudaStream_t st = as_stream(stream);
   g_launches += 2;
@@ -190,13 +194,14 @@ int gcge_block_cg_f32(int64_t n, const int32_t *rp, const int32_t *ci, const flo
 
 int gcge_borth_f64(int64_t n, const int32_t *Brp, const int32_t *Bci, const double *Bval,
                    const double *Q, int64_t ldq, int q, double *W, int64_t ldw, int m, int leaf,
-                   int *m_out, void *stream) {
+                   int orth, int *m_out, void *stream) {
   if (n < 1 || m < 0 || q < 0 || ldw < m || (q > 0 && (ldq < q || bad_ptr(Q))) || leaf < 1)
     return GCGE_EINVAL;
+  if (orth != GCGE_ORTH_ALG3 && orth != GCGE_ORTH_ALG2) return GCGE_EINVAL;
   if (m > 0 && bad_ptr(W)) return GCGE_EINVAL;
   const bool hasB = Brp != nullptr;
   if (hasB && (bad_ptr(Bci) || bad_ptr(Bval))) return GCGE_EINVAL;
-  return borth_standalone(n, Brp, Bci, Bval, Q, ldq, q, W, ldw, m, leaf, m_out,
+  return borth_standalone(n, Brp, Bci, Bval, Q, ldq, q, W, ldw, m, leaf, orth, m_out,
                           as_stream(stream));
 }
 

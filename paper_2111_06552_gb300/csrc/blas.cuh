@@ -20,6 +20,12 @@ template <typename T>
 int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
          double beta, double *C, int64_t ldc, int tc, Scratch &ws, cudaStream_t st);
 
+// The SIMT Gram kernels tile k in 32-column tiles on grid.y (at most 65535 tiles).
+inline bool gram_f64_grid_ok(int m, int k) {
+  (void)m;
+  return (k + 31) / 32 <= 65535;
+}
+
 // Same product as gram() for FP64 blocks, with a caller-owned partial-sum workspace of
 // `ws_doubles` doubles instead of an allocated one (fewer row splits when it is small).
 // Returns GCGE_EINVAL when even one split (m * k doubles) does not fit.

@@ -35,14 +35,16 @@ struct Slice {
 };
 
 // Per-column sums of a(row, j)^2 style reductions over a block -> part[blockIdx.x * k + j].
-template <int VEC>
-__device__ __forceinline__ void block_cols_to_part(const Slice<VEC> &sl, int k, const double (&acc)[VEC],
+// A thread's own sum is kept in the block's precision (FP32 blocks: the sums only steer
+// the inexact inner CG); the block and cross-CTA sums run in FP64, in a fixed order.
+template <int VEC, typename A>
+__device__ __forceinline__ void block_cols_to_part(const Slice<VEC> &sl, int k, const A (&acc)[VEC],
                                                    double *sred, double *part) {
   // sred: kCgThreads * VEC doubles laid out [row0][chunk*VEC + v] with row stride chunks*VEC
   const int w = sl.chunks * VEC;
   if (sl.on)
 #pragma unroll
-    for (int v = 0; v < VEC; ++v) sred[sl.row0 * w + sl.chunk * VEC + v] = acc[v];
+    for (int v = 0; v < VEC; ++v) sred[sl.row0 * w + sl.chunk * VEC + v] = (double)acc[v];
   __syncthreads();
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double s = 0.0;
@@ -84,9 +86,9 @@ cg_init_kernel(int64_t n, int k, const T *__restrict__ r, int64_t ld, double *__
                double rtol) {
   extern __shared__ double sm[];
   Slice<VEC> sl(k);
-  double acc[VEC];
+  T acc[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = 0.0;
+  for (int v = 0; v < VEC; ++v) acc[v] = T(0);
   if (sl.on) {
     for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
          row += (int64_t)gridDim.x * sl.rows_per_block) {
@@ -95,10 +97,10 @@ cg_init_kernel(int64_t n, int k, const T *__restrict__ r, int64_t ld, double *__
         T rv[VEC];
         ld_vec<T, VEC>(r + row * ld + j0, rv);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] += (double)rv[v] * (double)rv[v];
+        for (int v = 0; v < VEC; ++v) acc[v] += rv[v] * rv[v];
       } else {
         for (int v = 0; v < VEC && j0 + v < k; ++v) {
-          const double x = (double)r[row * ld + j0 + v];
+          const T x = r[row * ld + j0 + v];
           acc[v] += x * x;
         }
       }
@@ -133,9 +135,9 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
   }
   __syncthreads();
   Slice<VEC> sl(k);
-  double acc[VEC];
+  T acc[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = 0.0;
+  for (int v = 0; v < VEC; ++v) acc[v] = T(0);
   if (sl.on) {
     const int j0 = sl.chunk * VEC;
     T al[VEC];
@@ -154,7 +156,7 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
         for (int v = 0; v < VEC; ++v) {
           xv[v] += al[v] * pv[v];
           rv[v] -= al[v] * qv[v];
-          acc[v] += (double)rv[v] * (double)rv[v];
+          acc[v] += rv[v] * rv[v];
         }
         st_vec<T, VEC>(x + row * ldx + j0, xv);
         st_vec<T, VEC>(r + row * ld + j0, rv);
@@ -164,7 +166,7 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
           x[row * ldx + j] += al[v] * p[row * ld + j];
           const T rv = r[row * ld + j] - al[v] * q[row * ld + j];
           r[row * ld + j] = rv;
-          acc[v] += (double)rv * (double)rv;
+          acc[v] += rv * rv;
         }
       }
     }

@@ -1,5 +1,6 @@
 // Solver handle: gcge_create / gcge_solve / gcge_eigenpairs / gcge_stats_get / gcge_destroy.
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -330,8 +331,15 @@ int copy_out_staged(double *dst, int64_t ldv, const double *src, int64_t n, int 
   const int64_t piece = std::min<int64_t>(rows, (int64_t)1 << 20);   // doubles
   Staging sg;
   sg.st = st;
+  // GCGE_NO_PINNED_STAGING=1 takes the direct-copy branch below as if no pinned
+  // memory could be allocated (used by the tests of that branch)
+  static const bool no_pinned = [] {
+    const char *e = std::getenv("GCGE_NO_PINNED_STAGING");
+    return e && e[0] == '1';
+  }();
   for (int b = 0; b < 2; ++b) {
-    if (cudaHostAlloc(reinterpret_cast<void **>(&sg.buf[b]), sizeof(double) * piece,
+    if (no_pinned ||
+        cudaHostAlloc(reinterpret_cast<void **>(&sg.buf[b]), sizeof(double) * piece,
                       cudaHostAllocDefault) != cudaSuccess) {
       // no pinned memory to stage through: one direct copy
       (void)cudaGetLastError();
@@ -407,6 +415,8 @@ int gcge_options_default(gcge_options *o) {
   o->verbose = 0;
   o->checks = 0;
   o->profile = 0;
+  o->orth = GCGE_ORTH_ALG3;
+  o->max_proj_dim = 0;
   return GCGE_OK;
 }
 
@@ -425,7 +435,8 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
   else
     gcge_options_default(&h->opt);
   if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 ||
-      h->opt.mixed_bs2 < 0 ||
+      h->opt.mixed_bs2 < 0 || h->opt.max_proj_dim < 0 ||
+      (h->opt.orth != GCGE_ORTH_ALG3 && h->opt.orth != GCGE_ORTH_ALG2) ||
       (h->opt.precision != GCGE_FP64 && h->opt.precision != GCGE_MIXED)) {
     delete h;
     return GCGE_EINVAL;
@@ -437,6 +448,16 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
   h->tol = tol;
   h->moving = h->opt.moving == 1 || (h->opt.moving < 0 && nev >= 500);
   int sx = h->opt.size_x;
+  if (h->moving && h->opt.max_proj_dim > 0) {
+    // maxProjDim bounds [X, P, W]: the X window takes what P and W (bs each) leave
+    if (h->opt.max_proj_dim < 3 * block_size ||
+        (sx > 0 && sx != h->opt.max_proj_dim - 2 * block_size)) {
+      record_message("max_proj_dim must be >= 3 blockSize and agree with size_x");
+      delete h;
+      return GCGE_EINVAL;
+    }
+    sx = h->opt.max_proj_dim - 2 * block_size;
+  }
   if (sx <= 0) sx = h->moving ? 3 * block_size : nev + 3 * block_size;
   if (sx > A->n) sx = (int)A->n;
   if (sx < block_size || (!h->moving && sx < nev)) {
@@ -509,31 +530,33 @@ int gcge_eigenpairs(gcge_handle *h, double *evals, double *evecs, int64_t ldv, i
   for (int t = 0; t < h->nev; ++t) evals[t] = t < k ? h->lam[perm[t]] : NAN;
   if (nconv) *nconv = nl;
   if (evecs && k > 0) {
-    int *dperm = nullptr;
-    GCGE_CUDA(cudaMalloc(&dperm, sizeof(int) * k));
-    GCGE_CUDA(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * k, cudaMemcpyHostToDevice, h->st));
+    // device temporaries, freed on every exit path once the stream has drained
+    struct Temps {
+      int *dperm = nullptr;
+      double *tmp = nullptr;
+      cudaStream_t st = nullptr;
+      ~Temps() {
+        if (dperm || tmp) cudaStreamSynchronize(st);
+        if (dperm) cudaFree(dperm);
+        if (tmp) cudaFree(tmp);
+      }
+    } t;
+    t.st = h->st;
+    GCGE_CUDA(cudaMalloc(&t.dperm, sizeof(int) * k));
+    GCGE_CUDA(cudaMemcpyAsync(t.dperm, perm.data(), sizeof(int) * k, cudaMemcpyHostToDevice, h->st));
     double *dst = evecs;
-    double *tmp = nullptr;
     if (!evecs_on_device) {
-      GCGE_CUDA(cudaMalloc(&tmp, sizeof(double) * (size_t)h->n * k));
-      dst = tmp;
+      GCGE_CUDA(cudaMalloc(&t.tmp, sizeof(double) * (size_t)h->n * k));
+      dst = t.tmp;
     }
     const int64_t ldo = evecs_on_device ? ldv : h->n;
     int64_t g = ((int64_t)h->n * k + 255) / 256;
     if (g > 4096) g = 4096;
-    transpose_out_kernel<<<(int)g, 256, 0, h->st>>>(h->n, k, dperm, h->store, h->ld_store, dst, ldo);
+    transpose_out_kernel<<<(int)g, 256, 0, h->st>>>(h->n, k, t.dperm, h->store, h->ld_store, dst,
+                                                    ldo);
     GCGE_LAUNCH_CHECK();
     GCGE_CUDA(cudaStreamSynchronize(h->st));
-    if (!evecs_on_device) {
-      const int s = copy_out_staged(evecs, ldv, tmp, h->n, k, h->st);
-      if (s != GCGE_OK) {
-        cudaFree(dperm);
-        cudaFree(tmp);
-        return s;
-      }
-    }
-    cudaFree(dperm);
-    if (tmp) cudaFree(tmp);
+    if (!evecs_on_device) GCGE_CHECK(copy_out_staged(evecs, ldv, t.tmp, h->n, k, h->st));
   }
   return GCGE_OK;
 }

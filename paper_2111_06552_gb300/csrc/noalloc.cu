@@ -38,7 +38,10 @@ int scratch_address(double **out) {
     gcge::record_cuda_error(e, __FILE__, __LINE__);
     return GCGE_ECUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return GCGE_EINVAL;
+  if (dev < 0 || dev >= kMaxDevices) {
+    gcge::record_message("gcge_gram_f64_noalloc: device index beyond the 64 devices it serves");
+    return GCGE_EINVAL;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     void *p = nullptr;
@@ -64,6 +67,10 @@ extern "C" int gcge_gram_f64_noalloc(int64_t n, int m, int k, double alpha, cons
   if ((int64_t)m * k > (int64_t)GCGE_GRAM_NOALLOC_MAX_DOUBLES) {
     gcge::record_message(
         "gcge_gram_f64_noalloc: m * k exceeds GCGE_GRAM_NOALLOC_MAX_DOUBLES (static scratch)");
+    return GCGE_EINVAL;
+  }
+  if (!gcge::gram_f64_grid_ok(m, k)) {
+    gcge::record_message("gcge_gram_f64_noalloc: k needs more than 65535 column tiles");
     return GCGE_EINVAL;
   }
   double *ws = nullptr;

@@ -131,6 +131,17 @@ __global__ void gather_scale_kernel(int64_t n, int k, const int *__restrict__ id
   }
 }
 
+// x *= s (and bx *= s when bx is a separate column): one column of a row-major block.
+template <typename T>
+__global__ void scale_col_kernel(int64_t n, T *__restrict__ x, T *__restrict__ bx, int64_t ld,
+                                 double s) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    x[r * ld] = (T)((double)x[r * ld] * s);
+    if (bx) bx[r * ld] = (T)((double)bx[r * ld] * s);
+  }
+}
+
 // Abar assembly from its structure (left part and mirror of the Gram block).
 // Abar is d x d col-major (lda); columns [kp, d) hold G = V_a^T (A W) already.
 __global__ void assemble_abar_kernel(int d, int kx, int np, const double *__restrict__ lam,
@@ -302,6 +313,7 @@ class Engine {
 
   int64_t cg_steps = 0;
   int moves = 0;
+  int refills = 0;                 // reservoir vectors that joined the basis beside W
   double ms_step[7] = {0, 0, 0, 0, 0, 0, 0};
   double ms_syev = 0.0;
   double max_orth = 0.0, max_abar = 0.0;
@@ -455,6 +467,8 @@ class Engine {
   int normalize_drop(T *W, T *BW, int64_t ld, int m, double thr, int *m_out);
   int rec(T *W, T *BW, int64_t ld, int len, int c, int *out);
   int leaf(T *W, T *BW, int64_t ld, int len, int *out);
+  int alg2(T *W, T *BW, int64_t ld, int m, int *out);
+  int mgs_block(T *W, T *BW, int64_t ld, int m, int *out);
   int rayleigh_ritz(bool first, int d);
   int convergence(const T *X, int *c_out, int *chunk_start, int *chunk_len);
   int build_p(int d, int c, int bsn, int *np_out);
@@ -720,10 +734,106 @@ int Engine<T>::borth(T *W, int m, const QPart *parts, int nparts, int *m_out) {
     GCGE_CHECK(normalize_drop(W, BW, ld, m, th_.drop_tol, &mm));
     m = mm;
   }
-  const int c = std::max(1, std::min(std::min(m, h_->opt.orth_leaf), std::min(kLeaf, 1024)));
   int out = 0;
-  GCGE_CHECK(rec(W, BW, ld, m, c, &out));
+  if (h_->opt.orth == GCGE_ORTH_ALG2) {
+    GCGE_CHECK(alg2(W, BW, ld, m, &out));
+  } else {
+    const int c = std::max(1, std::min(std::min(m, h_->opt.orth_leaf), std::min(kLeaf, 1024)));
+    GCGE_CHECK(rec(W, BW, ld, m, c, &out));
+  }
   *m_out = out;
+  return GCGE_OK;
+}
+
+// Modified Gram-Schmidt inside one block of Algorithm 2, in the B inner product:
+// column j is scaled to unit B-norm and removed from the later columns of the block
+// at once.  A column whose B-norm fell to drop_tol (the block's columns started
+// Algorithm 2 at unit B-norm) is dependent: the block's rearmost column takes its
+// place (Section 3.1).  The pass repeats while the block's Gram differs from I by
+// more than leaf_tol.  Each column costs a global reduction read by the host, as
+// the paper counts for this method.
+template <typename T>
+int Engine<T>::mgs_block(T *W, T *BW, int64_t ld, int m, int *out) {
+  int mm = m;
+  for (int pass = 0; pass < th_.leaf_max && mm > 0; ++pass) {
+    int j = 0;
+    while (j < mm) {
+      g_launches += 2;
+      GCGE_CHECK(col_dots<T>(n_, 1, W + j, ld, BW + j, ld, d_norm2_, ws_, st_));
+      GCGE_CHECK(read_d(d_norm2_, h_d_, 1));
+      const double s = std::sqrt(std::max(h_d_[0], 0.0));
+      if (!(s > th_.drop_tol)) {
+        if (j < mm - 1) {
+          GCGE_CHECK(copyT(1, W + mm - 1, ld, W + j, ld));
+          if (!bI_) GCGE_CHECK(copyT(1, BW + mm - 1, ld, BW + j, ld));
+        }
+        --mm;
+        continue;
+      }
+      g_launches += 1;
+      scale_col_kernel<T><<<small_grid(n_), 256, 0, st_>>>(n_, W + j, bI_ ? nullptr : BW + j, ld,
+                                                          1.0 / s);
+      GCGE_LAUNCH_CHECK();
+      const int q = mm - j - 1;
+      if (q > 0) {   // r = (B x_j)^T X_later; X_later -= x_j r (and B X_later alike)
+        GCGE_CHECK(gramT(1, q, 1.0, BW + j, ld, W + j + 1, ld, 0.0, Rg_, ldR_));
+        GCGE_CHECK(vcT(1, q, -1.0, W + j, ld, Rg_, ldR_, 1.0, W + j + 1, ld));
+        if (!bI_) GCGE_CHECK(vcT(1, q, -1.0, BW + j, ld, Rg_, ldR_, 1.0, BW + j + 1, ld));
+      }
+      ++j;
+    }
+    if (mm == 0) break;
+    GCGE_CHECK(gramT(mm, mm, 1.0, W, ld, BW, ld, 0.0, t1_, dmax_));
+    g_launches += 1;
+    max_diff_kernel<<<1, 256, 0, st_>>>(mm, t1_, dmax_, nullptr, 0, 1, d_crit_);
+    GCGE_LAUNCH_CHECK();
+    GCGE_CHECK(read_d(d_crit_, h_d_, 1));
+    if (h_d_[0] <= th_.leaf_tol) break;
+  }
+  *out = mm;
+  return GCGE_OK;
+}
+
+// Algorithm 2 (modified block orthogonalisation, Section 3.1) on columns [0, m) of W
+// (BW alongside), after the deflation against [X_c, X, P]: blocks of
+// b = min(m/4, 200) columns; each block by modified Gram-Schmidt, then every later
+// column deflated against it (R = (B X_k)^T X_later, X_later -= X_k R, repeated
+// while R is relatively large).  Kept columns end up compacted at [0, *out).
+template <typename T>
+int Engine<T>::alg2(T *W, T *BW, int64_t ld, int m, int *out) {
+  const int b = std::max(1, std::min(m / 4, 200));
+  int pos = 0, mm = m;
+  while (pos < mm) {
+    const int bk = std::min(b, mm - pos);
+    int r = 0;
+    GCGE_CHECK(mgs_block(W + pos, BW + pos, ld, bk, &r));
+    const int later0 = pos + bk, nlater = mm - later0;
+    if (r < bk && nlater > 0) {   // dropped columns: the later ones move left
+      GCGE_CHECK(copyT(nlater, W + later0, ld, TMP_, ldW_));
+      GCGE_CHECK(copyT(nlater, TMP_, ldW_, W + pos + r, ld));
+      if (!bI_) {
+        GCGE_CHECK(copyT(nlater, BW + later0, ld, TMP_, ldW_));
+        GCGE_CHECK(copyT(nlater, TMP_, ldW_, BW + pos + r, ld));
+      }
+    }
+    mm -= bk - r;
+    const int rs = pos + r, nr = mm - rs;
+    if (r > 0 && nr > 0) {
+      for (int rep = 0; rep < th_.inner_max; ++rep) {
+        GCGE_CHECK(gramT(r, nr, 1.0, BW + pos, ld, W + rs, ld, 0.0, Rg_, ldR_));
+        g_launches += 3;
+        GCGE_CHECK(col_dots<T>(n_, nr, W + rs, ld, BW + rs, ld, d_norm2_, ws_, st_));
+        max_rel_kernel<<<1, 256, 0, st_>>>(r, nr, Rg_, ldR_, d_norm2_, d_crit_);
+        GCGE_LAUNCH_CHECK();
+        GCGE_CHECK(vcT(r, nr, -1.0, W + pos, ld, Rg_, ldR_, 1.0, W + rs, ld));
+        if (!bI_) GCGE_CHECK(vcT(r, nr, -1.0, BW + pos, ld, Rg_, ldR_, 1.0, BW + rs, ld));
+        GCGE_CHECK(read_d(d_crit_, h_d_, 1));
+        if (h_d_[0] <= th_.inner_tol) break;
+      }
+    }
+    pos += r;
+  }
+  *out = mm;
   return GCGE_OK;
 }
 
@@ -1085,6 +1195,7 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
         GCGE_CHECK(copy_cols<float, T>(n_, rres, res_ + res_next_, ldres_, TMP2_ + bsn, ldW_,
                                        nullptr, st_));
         res_next_ += rres;
+        refills += rres;
       }
     }
     QPart parts[2] = {{store_, ldS_, nlock_}, {V_[nxt] + xoff, ldV_, kxn + npn}};
@@ -1124,13 +1235,14 @@ template class Engine<float>;
 // ---------------------------------------------------------------- standalone B-orth
 int borth_standalone(int64_t n, const int32_t *Brp, const int32_t *Bci, const double *Bval,
                      const double *Q, int64_t ldq, int q, double *W, int64_t ldw, int m, int leaf,
-                     int *m_out, cudaStream_t st) {
+                     int orth, int *m_out, cudaStream_t st) {
   gcge_handle h;
   h.st = st;
   h.n = n;
   h.bs = 1;
   gcge_options_default(&h.opt);
   h.opt.orth_leaf = leaf;
+  h.opt.orth = orth;
   if (Brp) {
     h.B.n = n;
     h.B.rp = const_cast<int32_t *>(Brp);
@@ -1162,6 +1274,7 @@ void add_stats(gcge_handle *h, const Engine<T> &e) {
   h->stats.ms_syev += e.ms_syev;
   h->stats.cg_steps += e.cg_steps;
   h->stats.moves += e.moves;
+  h->stats.refills += e.refills;
   h->stats.max_orth_err = std::max(h->stats.max_orth_err, e.max_orth);
   h->stats.max_abar_err = std::max(h->stats.max_abar_err, e.max_abar);
   if (e.prof) {

@@ -32,7 +32,7 @@ inline const float *csr_vals<float>(const DevCsr &m) { return m.v32; }
 // B-orthonormalisation of a block through the C ABI (standalone buffers).
 int borth_standalone(int64_t n, const int32_t *Brp, const int32_t *Bci, const double *Bval,
                      const double *Q, int64_t ldq, int q, double *W, int64_t ldw, int m, int leaf,
-                     int *m_out, cudaStream_t st);
+                     int orth, int *m_out, cudaStream_t st);
 
 }  // namespace gcge
 

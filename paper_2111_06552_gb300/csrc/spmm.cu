@@ -17,11 +17,14 @@
 // from L2 once per nonzero.
 //
 // Optional fused epilogue (used by the CG step): per column j the dot product
-// sum_i X[i, j] (A X)[i, j].  Lanes holding the same columns reduce over the rows of
-// the warp with shuffles, then over the CTA with shared-memory atomic adds; every CTA
-// writes one partial row and the last CTA to finish (atomic ticket) sums the
-// partials in a fixed order into dot_out[0:k].  The order of the warps' atomic adds
-// is not fixed, so two runs can differ in the last bits of the dot products.
+// sum_i X[i, j] (A X)[i, j].  Each thread accumulates its own rows in the block's
+// precision (FP32 for FP32 blocks: the dot only steers the inexact inner CG); after
+// the row loop the lanes holding the same columns reduce over the warp's row groups
+// with shuffles (in FP64), each warp writes its own shared-memory slot, the warps'
+// slots are summed in warp order into the CTA's partial row, and the last CTA to
+// finish (atomic ticket) sums the partial rows in a fixed order into dot_out[0:k].
+// Every sum runs in a fixed order, so the dots are bitwise reproducible for a given
+// grid.
 #include "spmm.cuh"
 
 namespace gcge {
@@ -60,15 +63,16 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
             const T *__restrict__ val, int k, int G, T alpha, const T *__restrict__ X,
             int64_t ldx, T beta, T *__restrict__ Y, int64_t ldy, double *__restrict__ part,
             double *__restrict__ dot_out, unsigned *__restrict__ ticket, int64_t rows_per_cta) {
-  extern __shared__ double sdot[];   // k column sums, then blockDim.x reduction scratch
+  extern __shared__ double sdot[];   // per-warp column sums (warps x k), then blockDim.x scratch
   const int nchunks = (k + VEC - 1) / VEC;
   const int full = k / VEC;                 // chunks that are complete
   const int lane = threadIdx.x & 31;
   const int gl = lane & (G - 1);            // lane within the row group
-  if (DOT) {
-    for (int j = threadIdx.x; j < k; j += blockDim.x) sdot[j] = 0.0;
-    __syncthreads();
-  }
+  T dacc[DOT ? NV : 1][VEC];                // this thread's share of the fused dots
+#pragma unroll
+  for (int c = 0; c < (DOT ? NV : 1); ++c)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) dacc[c][v] = T(0);
   const int64_t rows_per_step = blockDim.x / G;
   const int64_t blk_end = min(n, (int64_t)(blockIdx.x + 1) * rows_per_cta);
   for (int64_t row = (int64_t)blockIdx.x * rows_per_cta + threadIdx.x / G;
@@ -163,26 +167,44 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
         }
       }
     }
-    if (DOT) {
-      // per column: X[row, j] * (A X)[row, j], reduced over the warp's rows by shuffles
+    if (DOT && live) {
+      // per column: X[row, j] * (A X)[row, j] into this thread's accumulators
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
         const int ch = gl + c * G;
+        if (ch < full) {
+          T xv[VEC];
+          load_chunk<T, VEC>(X + row * ldx + ch * VEC, xv);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          const int j = ch * VEC + v;
-          double d = 0.0;
-          if (live && ch < nchunks && j < k) d = (double)X[row * ldx + j] * (double)acc[c][v];
-          for (int o = G; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-          if (lane < G && ch < nchunks && j < k && d != 0.0) atomicAdd(&sdot[j], d);
+          for (int v = 0; v < VEC; ++v) dacc[c][v] += xv[v] * acc[c][v];
+        } else if (ch < nchunks) {
+          for (int v = 0; v < VEC && ch * VEC + v < k; ++v)
+            dacc[c][v] += __ldg(X + row * ldx + ch * VEC + v) * acc[c][v];
         }
       }
     }
   }
   if (DOT) {
+    // reduce over the warp's row groups (fixed butterfly order), one slot per warp
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const int ch = gl + c * G;
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        double d = (double)dacc[c][v];
+        for (int o = G; o < 32; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const int j = ch * VEC + v;
+        if (lane < G && ch < nchunks && j < k) sdot[warp * k + j] = d;
+      }
+    }
     __syncthreads();
-    for (int j = threadIdx.x; j < k; j += blockDim.x) part[(int64_t)blockIdx.x * k + j] = sdot[j];
-    last_cta_reduce(k, part, ticket, sdot + k, [&](int j, double v) { dot_out[j] = v; });
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += sdot[w * k + j];
+      part[(int64_t)blockIdx.x * k + j] = t;
+    }
+    last_cta_reduce(k, part, ticket, sdot + nwarps * k, [&](int j, double v) { dot_out[j] = v; });
   }
 }
 
@@ -223,12 +245,17 @@ void launch_v(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, c
   if (!carveout) {
     cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, true>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    // the fused dot keeps one k-wide slot per warp (k <= 1024: 66 KB)
+    cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (1024 * (kSpmmThreads / 32) + kSpmmThreads) * (int)sizeof(double));
     cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, false>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     carveout = true;
   }
   if (dot_out)
-    spmm_kernel<T, VEC, NV, true><<<pl.grid, kSpmmThreads, (k + kSpmmThreads) * sizeof(double), st>>>(
+    spmm_kernel<T, VEC, NV, true><<<pl.grid, kSpmmThreads,
+                                    (k * (kSpmmThreads / 32) + kSpmmThreads) * sizeof(double), st>>>(
         n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, pl.rows_per_cta);
   else
     spmm_kernel<T, VEC, NV, false><<<pl.grid, kSpmmThreads, 0, st>>>(

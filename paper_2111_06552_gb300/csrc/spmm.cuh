@@ -7,8 +7,8 @@ namespace gcge {
 // Y = alpha * A X + beta * Y.  When `dot_out` is non-null the kernel also forms, per
 // column j, sum_i X[i, j] * (A X)[i, j] into dot_out[j] (FP64): each CTA writes a
 // partial row of `part` (at least dot_blocks x k doubles) and the last CTA, chosen by
-// the atomic `ticket` (a zeroed unsigned, left zeroed), sums them in order.  Within a
-// CTA the warps add into shared memory atomically, in no fixed order.
+// the atomic `ticket` (a zeroed unsigned, left zeroed), sums them in order.  Every sum
+// runs in a fixed order, so the dots are bitwise reproducible for a given grid.
 template <typename T>
 int launch_spmm(int64_t n, const int32_t *rp, const int32_t *ci, const T *val, int k, T alpha,
                 const T *X, int64_t ldx, T beta, T *Y, int64_t ldy, double *dot_out,

@@ -225,8 +225,9 @@ def test_block_cg_f32(g):
     assert np.abs(host(Xd) - ref).max() <= 2e-4 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("orth", [0, 1])
 @pytest.mark.parametrize("m,q", [(1, 0), (5, 0), (20, 6), (37, 11)])
-def test_borth_matches_oracle(g, m, q):
+def test_borth_matches_oracle(g, m, q, orth):
     import torch
     p = W.make_config("q1grad_48", N=8, seed=5)
     n = p.n
@@ -237,11 +238,12 @@ def test_borth_matches_oracle(g, m, q):
         X[:, 3] = X[:, 0] - 2 * X[:, 1]                   # dependent inside the block
     if q and m >= 5:
         X[:, 4] = Q0 @ rng.standard_normal(q)             # inside span(Q0)
-    Y_ref, _ = O.b_orthonormalize(X, Q0, p.B)
+    # orth 0: Algorithm 3 (RecursiveOrthSVD); 1: Algorithm 2 (modified block orthogonalisation)
+    Y_ref, _ = (O.b_orthonormalize if orth == 0 else O.b_orthonormalize_alg2)(X, Q0, p.B)
     rp, ci, val = csr_dev(p.B)
     Wd = dev(padded(X, m))
     Qd = dev(Q0) if q else None
-    mo = g.gcge_borth_f64(n, rp, ci, val, Qd, q if q else 1, q, Wd, m, m, 16)
+    mo = g.gcge_borth_f64(n, rp, ci, val, Qd, q if q else 1, q, Wd, m, m, 16, orth)
     torch.cuda.synchronize()
     assert mo == Y_ref.shape[1]
     Y = host(Wd)[:, :mo]
@@ -251,6 +253,8 @@ def test_borth_matches_oracle(g, m, q):
         assert np.abs(Q0.T @ BY).max() < 1e-12
     cos = subspace_cos(Y, Y_ref, p.B)
     assert cos.min() > 1 - 1e-10
+    if orth == 1:   # Gram-Schmidt fixes the basis itself, column by column
+        assert np.abs(Y - Y_ref).max() <= 1e-8 * np.abs(Y_ref).max()
 
 
 def test_random_block_matches_generator(g):

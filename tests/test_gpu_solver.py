@@ -150,6 +150,42 @@ def test_mixed_precision_reaches_fp64_accuracy(g):
     assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
 
 
+@pytest.mark.parametrize("name,N,nev,bs,seed", [("fd2d", 20, 30, 4, 1), ("fd2d", 18, 40, 5, 2),
+                                                ("q1_160", 7, 24, 4, 3)])
+def test_mixed_moving_refill_matches_oracle(g, name, N, nev, bs, seed):
+    """Mixed precision with the moving mechanism (Section 3.3): the FP64 phase
+    starts from a window of 3 bs phase-1 vectors, refills it from the rest of them
+    as pairs lock, then moves as in the FP64 path.  Against the FP64 oracle (moving)."""
+    p = W.fd2d(N) if name == "fd2d" else W.make_config(name, N=N, seed=seed)
+    ev, X, st, status = _solve(g, p, nev, bs, seed=seed, precision=g.GCGE_MIXED, moving=1)
+    ref = G.gcg(p.A, p.B, nev, bs, 1e-8, W.initial_block(p.n, 3 * bs, seed),
+                G.Params(moving=True))
+    assert status == 0 and ref.converged
+    assert st["iterations_fp32"] > 0
+    assert st["refills"] > 0
+    assert np.abs(ev - ref.evals).max() <= 1e-8 * np.abs(ref.evals).max()
+    assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
+    Bx = X if p.B is None else p.B @ X
+    assert np.abs(X.T @ Bx - np.eye(nev)).max() < 1e-9
+    assert _check_vectors(X, ev, p.A, p.B) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solver_alg2_matches_oracle(g, precision):
+    """STEP 2 by Algorithm 2 (modified block orthogonalisation) in place of Algorithm 3,
+    FP64 and mixed, against the oracle run with Algorithm 2."""
+    p = W.make_config("q1_160", N=6, seed=3)
+    nev, bs = 16, 4
+    X0 = W.initial_block(p.n, nev + 3 * bs, 7)
+    ev, X, st, status = _solve(g, p, nev, bs, X0, orth=g.GCGE_ORTH_ALG2, precision=precision)
+    ref = G.gcg(p.A, p.B, nev, bs, 1e-8, X0, G.Params(orth_alg=2))
+    assert status == 0 and ref.converged
+    assert np.abs(ev - ref.evals).max() <= 1e-8 * np.abs(ref.evals).max()
+    assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
+    assert np.abs(X.T @ (p.B @ X) - np.eye(nev)).max() < 1e-10
+    assert _check_vectors(X, ev, p.A, p.B) <= 1e-6
+
+
 @pytest.mark.parametrize("kind", ["permuted", "diagonal"])
 def test_union_pattern_differs_from_a(g, kind):
     """S = A - theta B on a union pattern that is not A's own: B = P A P^T (same nnz,
