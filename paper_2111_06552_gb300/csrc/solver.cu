@@ -329,8 +329,11 @@ class Engine {
   // Reservoir of start vectors (FP32, n x nres, ascending): the X window is filled from
   // its first columns and, as pairs lock, refilled from the next ones, which enter the
   // iteration beside W (so their rows of Abar come from the Gram product).
+  // set before setup() when a reservoir will be given: W then holds up to
+  // max(sizeX, 2 blockSize) columns and A W is sized for that
+  bool reservoir_planned = false;
   void set_reservoir(const float *Z, int64_t ldz, int nz) {
-    res_ = Z;
+    res_ = reservoir_planned ? Z : nullptr;
     ldres_ = ldz;
     nres_ = nz;
   }
@@ -351,7 +354,8 @@ class Engine {
   T *store_ = nullptr;             // locked vectors, ldS_
   int64_t ldS_ = 0;
   int store_cap_ = 0;
-  T *AW_ = nullptr;                // A W, ldB_
+  T *AW_ = nullptr;                // A W, ldAW_ (W may hold reservoir vectors beside blockSize)
+  int64_t ldAW_ = 0;
   T *R0_ = nullptr;                // CG initial residual, ldB_
   int64_t ldB_ = 0;
   T *BWb_ = nullptr, *TMP_ = nullptr, *TMP2_ = nullptr;   // ldW_
@@ -526,6 +530,7 @@ int Engine<T>::setup(int size_x, int nev, int store_cap, int bs) {
   store_cap_ = std::max(store_cap, 1);
   ldS_ = round_up(store_cap_, 4);
   ldB_ = round_up(bs_, 4);
+  ldAW_ = reservoir_planned ? round_up(std::max(sizeX_, 2 * bs_), 4) : ldB_;
   ldW_ = round_up(std::max(sizeX_, 2 * bs_), 4);
   ldC_ = round_up(2 * bs_, 4);
   ldR_ = ldS_ + ldV_;
@@ -534,7 +539,7 @@ int Engine<T>::setup(int size_x, int nev, int store_cap, int bs) {
   GCGE_CHECK(alloc_dev((void **)&V_[0], ts * n * ldV_));
   GCGE_CHECK(alloc_dev((void **)&V_[1], ts * n * ldV_));
   GCGE_CHECK(alloc_dev((void **)&store_, ts * n * ldS_));
-  GCGE_CHECK(alloc_dev((void **)&AW_, ts * n * ldB_));
+  GCGE_CHECK(alloc_dev((void **)&AW_, ts * n * ldAW_));
   GCGE_CHECK(alloc_dev((void **)&R0_, ts * n * ldB_));
   GCGE_CHECK(alloc_dev((void **)&BWb_, ts * n * ldW_));
   GCGE_CHECK(alloc_dev((void **)&TMP_, ts * n * ldW_));
@@ -866,8 +871,12 @@ int Engine<T>::rayleigh_ritz(bool first, int d) {
     // structure of Eq. (struct_bar_A_new): only [X_a, P, W]^T (A W) is a large product
     const int kp = kx_ + np_;
     T *W = Va + kp;
-    GCGE_CHECK(spA(W, ldV_, nw_, AW_, ldB_));
-    GCGE_CHECK(gramT(d, nw_, 1.0, Va, ldV_, AW_, ldB_, 0.0, Abar_ + (int64_t)kp * lda, lda));
+    if (nw_ > ldAW_) {
+      record_message("W is wider than its A W buffer");
+      return GCGE_EINVAL;
+    }
+    GCGE_CHECK(spA(W, ldV_, nw_, AW_, ldAW_));
+    GCGE_CHECK(gramT(d, nw_, 1.0, Va, ldV_, AW_, ldAW_, 0.0, Abar_ + (int64_t)kp * lda, lda));
     assemble_abar_kernel<<<small_grid((int64_t)d * kp), 256, 0, st_>>>(d, kx_, np_, lam_, a0_, bs_,
                                                                        Abar_, lda);
     GCGE_LAUNCH_CHECK();
@@ -1187,6 +1196,17 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     if (res_ && res_next_ < nres_ && kxn < sizeX_) {
       rres = std::min(nres_ - res_next_, sizeX_ - kxn);
       rres = std::min(rres, (int)ldW_ - bsn);
+      if (xoff > 0 && xoff + kxn + npn + bsn + rres > dmax_) {
+        // the columns in front of X_a were locked (they are in the store): move
+        // [X_a, P] to column 0 so that the refill fits behind W
+        GCGE_CHECK(copyT(kxn, V_[nxt] + xoff, ldV_, TMP_, ldW_));
+        GCGE_CHECK(copyT(kxn, TMP_, ldW_, V_[nxt], ldV_));
+        if (npn > 0) {
+          GCGE_CHECK(copyT(npn, V_[nxt] + xoff + kxn, ldV_, TMP_, ldW_));
+          GCGE_CHECK(copyT(npn, TMP_, ldW_, V_[nxt] + kxn, ldV_));
+        }
+        xoff = 0;
+      }
       // the next basis [X_a, P, W] starts at column xoff of V[nxt] and must end by dmax_
       rres = std::min(rres, dmax_ - (xoff + kxn + npn + bsn));
       rres = std::max(rres, 0);
@@ -1378,6 +1398,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     // and P (STEP 5) is built as in the plain path
     e2.use_p = h->moving || !p1_all;
     if (h->opt.profile) e2.prof = &prof;
+    e2.reservoir_planned = true;
     s = e2.setup(sx, h->nev, h->store_cap, bs2);
     if (s == GCGE_OK) {
       e2.set_reservoir(Z, ldz, nz);

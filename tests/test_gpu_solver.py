@@ -150,14 +150,19 @@ def test_mixed_precision_reaches_fp64_accuracy(g):
     assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
 
 
-@pytest.mark.parametrize("name,N,nev,bs,seed", [("fd2d", 20, 30, 4, 1), ("fd2d", 18, 40, 5, 2),
+@pytest.mark.parametrize("name,N,nev,bs,seed", [("fd2d", 10, 24, 4, 1), ("fd2d", 14, 30, 5, 1),
+                                                ("fd2d", 18, 40, 5, 1), ("q1_160", 6, 30, 5, 3),
                                                 ("q1_160", 7, 24, 4, 3)])
 def test_mixed_moving_refill_matches_oracle(g, name, N, nev, bs, seed):
     """Mixed precision with the moving mechanism (Section 3.3): the FP64 phase
     starts from a window of 3 bs phase-1 vectors, refills it from the rest of them
-    as pairs lock, then moves as in the FP64 path.  Against the FP64 oracle (moving)."""
+    as pairs lock, then moves as in the FP64 path.  Against the FP64 oracle (moving).
+    The FP32 phase's switch tolerance is raised to 1e-3 so that it locks pairs on
+    these small pencils (their FP32 floor lies above the default 3e-6), which gives
+    the FP64 phase phase-1 vectors beyond its window to refill from."""
     p = W.fd2d(N) if name == "fd2d" else W.make_config(name, N=N, seed=seed)
-    ev, X, st, status = _solve(g, p, nev, bs, seed=seed, precision=g.GCGE_MIXED, moving=1)
+    ev, X, st, status = _solve(g, p, nev, bs, seed=seed, precision=g.GCGE_MIXED, moving=1,
+                               mixed_switch_tol=1e-3)
     ref = G.gcg(p.A, p.B, nev, bs, 1e-8, W.initial_block(p.n, 3 * bs, seed),
                 G.Params(moving=True))
     assert status == 0 and ref.converged
@@ -241,6 +246,45 @@ def test_eigenpairs_leading_dimensions(g):
     assert np.array_equal(dh[:, :n].T, X)
     assert np.all(dh[:, n:] == -7.0)
     s.close()
+
+
+_DIRECT_COPY_SCRIPT = r"""
+import ctypes as C, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import paper_2111_06552_gb300 as g
+import workloads as W
+p = W.fd2d(16)
+nev, n = 12, p.n
+s = g.Solver(p.A, None, nev, 4, 1e-8, seed=4)
+ev, _ = s.solve()
+ref = np.zeros((nev, n))
+nc = C.c_int(0)
+ev0 = np.zeros(nev)
+# ldv == n: one flat copy; ldv > n: padding rows left untouched
+assert g.lib().gcge_eigenpairs(s.h, ev0.ctypes.data, ref.ctypes.data, n, 0, C.byref(nc)) == 0
+out = np.full((nev, n + 5), -7.0)
+assert g.lib().gcge_eigenpairs(s.h, ev0.ctypes.data, out.ctypes.data, n + 5, 0, C.byref(nc)) == 0
+assert np.array_equal(out[:, :n], ref) and np.all(out[:, n:] == -7.0)
+res = np.linalg.norm(p.A @ ref.T - ref.T * ev0, axis=0) / ev0
+assert res.max() < 1e-8, res.max()
+s.close()
+print("direct copy ok")
+"""
+
+
+def test_eigenpairs_without_pinned_staging(g):
+    """The copy-out branch taken when no pinned staging memory can be allocated
+    (forced by GCGE_NO_PINNED_STAGING=1, read once per process: a child process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, GCGE_NO_PINNED_STAGING="1")
+    r = subprocess.run([sys.executable, "-c", _DIRECT_COPY_SCRIPT, root], env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "direct copy ok" in r.stdout
 
 
 def test_not_converged_returns_partial(g):

@@ -46,6 +46,10 @@ def _simulate(rng, size_x, bs, nev, moving, nres, iters=400):
         if nres and res_next < nres and kxn < size_x:
             rres = min(nres - res_next, size_x - kxn)
             rres = min(rres, ldW - bsn)
+            if xoff > 0 and xoff + kxn + npn + bsn + rres > dmax:
+                # [X_a, P] move to column 0 (staged through a buffer of width ldW)
+                assert kxn <= ldW and npn <= ldW
+                xoff = 0
             rres = min(rres, dmax - (xoff + kxn + npn + bsn))
             rres = max(rres, 0)
             res_next += rres
@@ -92,3 +96,19 @@ def test_old_refill_bound_overflowed():
         if xoff + kxn + npn + nwn > dmax:
             hit += 1
     assert hit > 0
+
+
+def test_refill_keeps_the_window_full():
+    """With P and W at full width, pairs that lock free window slots at the front of
+    the buffer; the refill must still reach them (the window does not shrink while
+    phase-1 vectors are left)."""
+    bs, nev = 4, 40
+    size_x = 3 * bs
+    dmax, ldW = size_x + 2 * bs, size_x
+    kx, c, npn, bsn = size_x, 3, bs, bs
+    xoff, kxn = c, kx - c
+    rres = min(100, size_x - kxn, ldW - bsn)
+    if xoff > 0 and xoff + kxn + npn + bsn + rres > dmax:
+        xoff = 0
+    rres = min(rres, dmax - (xoff + kxn + npn + bsn))
+    assert kxn + rres == size_x
