@@ -233,6 +233,24 @@ int gcge_vc_f32(int64_t n, int d, int q, double alpha, const float *d_V, int64_t
                 const double *d_C, int64_t ldc, double beta, float *d_Y, int64_t ldy,
                 int tc, void *stream);
 
+/* The same FP64 products on the bf16 tensor cores (not in the paper: GB300 runs FP64
+ * FMA at 1/64 of its FP32 rate).  Along the reduction dimension the operands are cut
+ * into windows of 128 entries; each row of an operand gets one exponent per window
+ * and is written as seven signed 7-bit digits (49 bits); the 28 digit-plane products
+ * with the largest scales run as tcgen05 bf16 MMAs whose seven scale groups
+ * accumulate exactly in FP32, and each window is summed into FP64.  The error of an
+ * entry is about 2^-47 * 128 * sum over windows of max|x| max|y| (the window
+ * maxima of the two operands), against about 2^-53 sqrt(n) sum |x||y| for the FP64
+ * kernels.  Same arguments and layouts as gcge_gram_f64 / gcge_vc_f64; scratch
+ * (about 14 bytes per operand entry, bounded per pass) is allocated
+ * stream-ordered and freed before return.  n <= 2^30. */
+int gcge_gram_f64_tc(int64_t n, int m, int k, double alpha, const double *d_X, int64_t ldx,
+                     const double *d_Y, int64_t ldy, double beta, double *d_C, int64_t ldc,
+                     void *stream);
+int gcge_vc_f64_tc(int64_t n, int d, int q, double alpha, const double *d_V, int64_t ldv,
+                   const double *d_C, int64_t ldc, double beta, double *d_Y, int64_t ldy,
+                   void *stream);
+
 /* Status of the tensor-core kernels (tc != 0 above, and the solver's FP32 phase):
  * synchronises `stream`, returns GCGE_ETIMEOUT if a kernel's bounded internal wait
  * ran out since the last call (that launch's output is invalid; the flag is then

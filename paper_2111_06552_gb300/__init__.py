@@ -102,6 +102,8 @@ _SIGS = {
     "gcge_random_block_f64": (_I, [_I64, _I, C.c_uint64, _P, _I64, _P]),
     "gcge_tc_status": (_I, [_P]),
     "gcge_gram_f64_noalloc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
+    "gcge_gram_f64_tc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
+    "gcge_vc_f64_tc": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
 }
 GCGE_GRAM_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
 
@@ -173,6 +175,16 @@ def gcge_gram_f64_noalloc(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, stream=
     return _check(lib().gcge_gram_f64_noalloc(n, m, k, alpha, _addr(X), ldx, _addr(Y), ldy, beta,
                                               _addr(Cm), ldc, _stream(stream)),
                   "gcge_gram_f64_noalloc")
+
+
+def gcge_gram_f64_tc(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, stream=None):
+    _check(lib().gcge_gram_f64_tc(n, m, k, alpha, _addr(X), ldx, _addr(Y), ldy, beta, _addr(Cm),
+                                  ldc, _stream(stream)), "gcge_gram_f64_tc")
+
+
+def gcge_vc_f64_tc(n, d, q, alpha, V, ldv, Cm, ldc, beta, Y, ldy, stream=None):
+    _check(lib().gcge_vc_f64_tc(n, d, q, alpha, _addr(V), ldv, _addr(Cm), ldc, beta, _addr(Y),
+                                ldy, _stream(stream)), "gcge_vc_f64_tc")
 
 
 def gcge_gram_f32(n, m, k, alpha, X, ldx, Y, ldy, beta, Cm, ldc, tc=1, stream=None):

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgcge.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["spmm.cu", "blas.cu", "tc.cu", "tc_tma.cu", "cg.cu", "syev.cu", "syev_mp.cu", "solver.cu", "handle.cu",
-           "api.cu", "grad.cu", "noalloc.cu"]
+           "api.cu", "grad.cu", "noalloc.cu", "oz.cu"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          ARCH, "-I", os.path.join(ROOT, "include")]
 

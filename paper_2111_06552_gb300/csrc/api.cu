@@ -136,6 +136,38 @@ int gcge_vc_f64(int64_t n, int d, int q, double alpha, const double *V, int64_t 
   return vc<double>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, 0, as_stream(stream));
 }
 
+int gcge_gram_f64_tc(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx,
+                     const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
+                     void *stream) {
+  if (n < 0 || m < 0 || k < 0 || ldx < m || ldy < k || ldc < m) return GCGE_EINVAL;
+  if (m == 0 || k == 0) return GCGE_OK;
+  if (bad_ptr(C) || (n > 0 && (bad_ptr(X) || bad_ptr(Y)))) return GCGE_EINVAL;
+  cudaStream_t st = as_stream(stream);
+  if (n == 0) return gcge_gram_f64(n, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, stream);
+  Scratch ws;
+  g_launches += 4;
+  const int s = oz_gram(n, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, ws, st);
+  ws.release(st);
+  if (s == GCGE_EINVAL) record_message("gcge_gram_f64_tc: shape outside the emulated kernel");
+  return s;
+}
+
+int gcge_vc_f64_tc(int64_t n, int d, int q, double alpha, const double *V, int64_t ldv,
+                   const double *C, int64_t ldc, double beta, double *Y, int64_t ldy,
+                   void *stream) {
+  if (n < 0 || d < 0 || q < 0 || ldv < d || ldc < d || ldy < q) return GCGE_EINVAL;
+  if (q == 0 || n == 0) return GCGE_OK;
+  if (bad_ptr(Y) || (d > 0 && (bad_ptr(V) || bad_ptr(C)))) return GCGE_EINVAL;
+  if (d == 0) return gcge_vc_f64(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, stream);
+  cudaStream_t st = as_stream(stream);
+  Scratch ws;
+  g_launches += 3;
+  const int s = oz_vc(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, ws, st);
+  ws.release(st);
+  if (s == GCGE_EINVAL) record_message("gcge_vc_f64_tc: shape outside the emulated kernel");
+  return s;
+}
+
 int gcge_vc_f32(int64_t n, int d, int q, double alpha, const float *V, int64_t ldv,
                 const double *C, int64_t ldc, double beta, float *Y, int64_t ldy, int tc,
                 void *stream) {

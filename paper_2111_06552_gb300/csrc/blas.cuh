@@ -33,6 +33,14 @@ int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, i
                        const double *Y, int64_t ldy, double beta, double *C, int64_t ldc,
                        double *ws, int64_t ws_doubles, cudaStream_t st);
 
+// FP64 Gram and V C on the bf16 tensor cores from exact 7-bit digit slices (oz.cu):
+// same arguments and layouts as gram<double> / vc<double>.  GCGE_EINVAL when the shape
+// is outside what the kernels take (n > 2^30, no tensor-map encoder).
+int oz_gram(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx, const double *Y,
+            int64_t ldy, double beta, double *C, int64_t ldc, Scratch &ws, cudaStream_t st);
+int oz_vc(int64_t n, int d, int q, double alpha, const double *V, int64_t ldv, const double *C,
+          int64_t ldc, double beta, double *Y, int64_t ldy, Scratch &ws, cudaStream_t st);
+
 // Y(n x q) = alpha * V(n x d) C(d x q col-major FP64) + beta * Y.
 // `ws` (optional) holds the split operand of the tensor-core path.
 template <typename T>
