@@ -88,6 +88,9 @@ typedef struct {
   int orth;                 /* STEP 2 orthogonaliser: GCGE_ORTH_ALG3 (RecursiveOrthSVD,
                                Algorithm 3) or GCGE_ORTH_ALG2 (modified block
                                orthogonalisation, Algorithm 2), Section 3.1        (ALG3) */
+  int fp64_emulation;       /* 1: large FP64 Gram and V C products run on the bf16 tensor
+                               cores from exact digit slices (gcge_gram_f64_tc); 0: the
+                               FP64 kernels only                                       (1)   */
   int max_proj_dim;         /* moving mechanism (Section 3.3): largest dimension of the
                                projection subspace [X, P, W]; the X window is then
                                max_proj_dim - 2 blockSize columns. 0: 5 blockSize.
@@ -108,7 +111,9 @@ typedef struct {
 #define GCGE_K_SPMM64 6       /* FP64 SpMM                                                */
 #define GCGE_K_GRAM64 7       /* FP64 Gram                                                */
 #define GCGE_K_VC64 8         /* FP64 V C                                                 */
-#define GCGE_K_CLASSES 9
+#define GCGE_K_GRAM64TC 9     /* FP64 Gram on the bf16 tensor cores (digit slices)        */
+#define GCGE_K_VC64TC 10      /* FP64 V C on the bf16 tensor cores (digit slices)         */
+#define GCGE_K_CLASSES 11
 
 /* Per-solve statistics (times are CUDA-event milliseconds on the handle's stream). */
 typedef struct {

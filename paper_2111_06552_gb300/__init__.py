@@ -36,7 +36,8 @@ GCGE_FP64 = 0
 GCGE_MIXED = 1
 GCGE_ORTH_ALG3 = 0
 GCGE_ORTH_ALG2 = 1
-KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other", "spmm64", "gram64", "vc64")
+KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other", "spmm64", "gram64", "vc64",
+                  "gram64tc", "vc64tc")
 
 
 class GcgeError(RuntimeError):
@@ -58,7 +59,8 @@ class gcge_options(C.Structure):
                 ("size_x", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("initial_block", C.c_void_p), ("mixed_switch_tol", C.c_double),
                 ("verbose", C.c_int), ("checks", C.c_int), ("profile", C.c_int),
-                ("mixed_bs2", C.c_int), ("orth", C.c_int), ("max_proj_dim", C.c_int)]
+                ("mixed_bs2", C.c_int), ("orth", C.c_int), ("fp64_emulation", C.c_int),
+                ("max_proj_dim", C.c_int)]
 
 
 class gcge_stats(C.Structure):

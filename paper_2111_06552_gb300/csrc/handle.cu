@@ -416,6 +416,7 @@ int gcge_options_default(gcge_options *o) {
   o->checks = 0;
   o->profile = 0;
   o->orth = GCGE_ORTH_ALG3;
+  o->fp64_emulation = 1;
   o->max_proj_dim = 0;
   return GCGE_OK;
 }

@@ -425,52 +425,61 @@ struct Carve {
   }
 };
 
-constexpr size_t kPlaneBudget = (size_t)16 << 30;   // bytes of A planes per pass
+constexpr size_t kPlaneBudget = (size_t)4 << 30;    // bytes of digit planes per pass
 
 }  // namespace
 
 // C(m x k, col-major ldc) = alpha X^T Y + beta C with X n x m, Y n x k row-major FP64.
+// The rows are taken in chunks and the columns of X in groups of 128-column tiles so that
+// the planes of one pass stay within kPlaneBudget; every CTA adds its share of each
+// chunk into its own partial block, reduced at the end in a fixed order.
 int oz_gram(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx, const double *Y,
             int64_t ldy, double beta, double *C, int64_t ldc, Scratch &ws, cudaStream_t st) {
   if (m <= 0 || k <= 0) return GCGE_OK;
   if (n <= 0 || n > ((int64_t)1 << 30)) return GCGE_EINVAL;
-  const int64_t Kp = round_up(n, kWin);
-  const int nwin = (int)(Kp / kWin);
   int N = 0, ntiles = 0;
   n_tiling(k, &N, &ntiles);
   const int RpB = (int)round_up((int64_t)ntiles * N, kSlRows);   // slicing works in row tiles
   const int mtiles_all = (m + 127) / 128;
-  const size_t per_tile = (size_t)kDigits * 128 * Kp * 2;
-  int mchunk = (int)std::max<size_t>(1, kPlaneBudget / per_tile);
-  mchunk = std::min(mchunk, mtiles_all);
+  const int mchunk = std::min(mtiles_all, 4);
   const int RpA = mchunk * 128;
+  const int64_t bytes_per_row = (int64_t)kDigits * 2 * (RpA + RpB);
+  int64_t nc = std::max<int64_t>(kWin, (int64_t)(kPlaneBudget / bytes_per_row) / kWin * kWin);
+  nc = std::min(nc, round_up(n, kWin));
+  const int nwc = (int)(nc / kWin);                 // windows per row chunk
   const int sm_count = device_sm_count();
   int splits = std::max(1, sm_count / std::max(1, mchunk * ntiles));
-  splits = std::min(splits, nwin);
-  const int wps = (nwin + splits - 1) / splits;
-  splits = (nwin + wps - 1) / wps;
-  const size_t bytes = (size_t)kDigits * RpB * Kp * 2 + (size_t)nwin * RpB * 4 +
-                       (size_t)kDigits * RpA * Kp * 2 + (size_t)nwin * RpA * 4 +
+  splits = std::min(splits, nwc);
+  const size_t bytes = (size_t)kDigits * RpB * nc * 2 + (size_t)nwc * RpB * 4 +
+                       (size_t)kDigits * RpA * nc * 2 + (size_t)nwc * RpA * 4 +
                        (size_t)splits * m * k * 8 + 8 * 1024;
   void *wsp = nullptr;
   GCGE_CHECK(ws.get(bytes, st, &wsp));
   Carve cv{static_cast<unsigned char *>(wsp)};
-  uint16_t *PB = cv.take<uint16_t>((size_t)kDigits * RpB * Kp);
-  int *EBt = cv.take<int>((size_t)nwin * RpB);
-  uint16_t *PA = cv.take<uint16_t>((size_t)kDigits * RpA * Kp);
-  int *EAt = cv.take<int>((size_t)nwin * RpA);
+  uint16_t *PB = cv.take<uint16_t>((size_t)kDigits * RpB * nc);
+  int *EBt = cv.take<int>((size_t)nwc * RpB);
+  uint16_t *PA = cv.take<uint16_t>((size_t)kDigits * RpA * nc);
+  int *EAt = cv.take<int>((size_t)nwc * RpA);
   double *part = cv.take<double>((size_t)splits * m * k);
-  // Y: rows of the B planes are the columns of Y, reduction over the rows of Y
-  GCGE_CHECK(slice(Y, 1, ldy, k, n, RpB, Kp, PB, EBt, st));
   CUtensorMap mb, ma;
-  if (!plane_map(&mb, PB, RpB, Kp, N) || !plane_map(&ma, PA, RpA, Kp, 128)) return GCGE_EINVAL;
-  for (int t0 = 0; t0 < mtiles_all; t0 += mchunk) {
-    const int tiles = std::min(mchunk, mtiles_all - t0);
-    const int c0 = t0 * 128, cols = std::min(m - c0, tiles * 128);
-    GCGE_CHECK(slice(X + c0, 1, ldx, cols, n, RpA, Kp, PA, EAt, st));
-    // partial D of this column chunk: part[split][j][c0 + i]
-    GCGE_CHECK(gemm_launch(ma, mb, EAt, RpA, EBt, RpB, N, nwin, wps, splits, tiles, ntiles, 0,
-                           cols, k, 1.0, 0.0, part + c0, 1, m, (int64_t)m * k, st));
+  if (!plane_map(&mb, PB, RpB, nc, N) || !plane_map(&ma, PA, RpA, nc, 128)) return GCGE_EINVAL;
+  for (int64_t r0 = 0; r0 < n; r0 += nc) {
+    const int64_t rows = std::min(nc, n - r0);
+    const int nwin = (int)((rows + kWin - 1) / kWin);
+    const int wps = (nwin + splits - 1) / splits;
+    const int used = (nwin + wps - 1) / wps;          // CTAs with windows; the rest add zero
+    (void)used;
+    // Y: rows of the B planes are the columns of Y, reduction over the rows of Y
+    GCGE_CHECK(slice(Y + r0 * ldy, 1, ldy, k, rows, RpB, nc, PB, EBt, st));
+    for (int t0 = 0; t0 < mtiles_all; t0 += mchunk) {
+      const int tiles = std::min(mchunk, mtiles_all - t0);
+      const int c0 = t0 * 128, cols = std::min(m - c0, tiles * 128);
+      GCGE_CHECK(slice(X + r0 * ldx + c0, 1, ldx, cols, rows, RpA, nc, PA, EAt, st));
+      // part[split][j][c0 + i] += this chunk's share (overwritten by the first chunk)
+      GCGE_CHECK(gemm_launch(ma, mb, EAt, RpA, EBt, RpB, N, nwin, wps, splits, tiles, ntiles, 0,
+                             cols, k, 1.0, r0 == 0 ? 0.0 : 1.0, part + c0, 1, m, (int64_t)m * k,
+                             st));
+    }
   }
   return gram_reduce_launch(m, k, splits, part, alpha, beta, C, ldc, st);
 }

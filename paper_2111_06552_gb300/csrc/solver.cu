@@ -332,6 +332,8 @@ class Engine {
   // set before setup() when a reservoir will be given: W then holds up to
   // max(sizeX, 2 blockSize) columns and A W is sized for that
   bool reservoir_planned = false;
+  // FP64 engine: keep the locked vectors in the handle's store (no second n x nev copy)
+  bool share_store = false;
   void set_reservoir(const float *Z, int64_t ldz, int nz) {
     res_ = reservoir_planned ? Z : nullptr;
     ldres_ = ldz;
@@ -352,6 +354,7 @@ class Engine {
   int64_t ldV_ = 0;
   int cur_ = 0;
   T *store_ = nullptr;             // locked vectors, ldS_
+  bool store_shared_ = false;      // store_ is the handle's FP64 store (not freed here)
   int64_t ldS_ = 0;
   int store_cap_ = 0;
   T *AW_ = nullptr;                // A W, ldAW_ (W may hold reservoir vectors beside blockSize)
@@ -444,17 +447,35 @@ class Engine {
     if (sizeof(T) == 4) return c;
     return c == GCGE_K_SPMM ? GCGE_K_SPMM64 : c == GCGE_K_GRAM ? GCGE_K_GRAM64 : GCGE_K_VC64;
   }
+  // FP64 products of at least this size run on the bf16 tensor cores from exact digit
+  // slices (oz.cu); smaller ones cost less in the FP64 kernels than their slicing
+  bool emulate(int64_t a, int64_t b) const {
+    return sizeof(T) == 8 && h_->opt.fp64_emulation && n_ >= 16384 && a * b >= 2048 && a >= 8 &&
+           b >= 8;
+  }
   int gramT(int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
             double beta, double *C, int64_t ldc) {
+    if (emulate(m, k)) {
+      g_launches += 5;
+      ProfScope ps(prof, GCGE_K_GRAM64TC, (double)n_ * (m + k) * sizeof(T), 2.0 * n_ * m * k);
+      return oz_gram(n_, m, k, alpha, (const double *)X, ldx, (const double *)Y, ldy, beta, C,
+                     ldc, ws_, st_);
+    }
     g_launches += 2;
     ProfScope ps(prof, cls(GCGE_K_GRAM), (double)n_ * (m + k) * sizeof(T), 2.0 * n_ * m * k);
     return gram<T>(n_, m, k, alpha, X, ldx, Y, ldy, beta, C, ldc, use_tc(), ws_, st_);
   }
   int vcT(int d, int q, double alpha, const T *V, int64_t ldv, const double *C, int64_t ldc,
           double beta, T *Y, int64_t ldy) {
+    const double vbytes = (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T);
+    if (emulate(d, q)) {
+      g_launches += 3;
+      ProfScope ps(prof, GCGE_K_VC64TC, vbytes, 2.0 * n_ * d * q);
+      return oz_vc(n_, d, q, alpha, (const double *)V, ldv, C, ldc, beta, (double *)Y, ldy, ws_,
+                   st_);
+    }
     g_launches += 1;
-    ProfScope ps(prof, cls(GCGE_K_VC), (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T),
-                 2.0 * n_ * d * q);
+    ProfScope ps(prof, cls(GCGE_K_VC), vbytes, 2.0 * n_ * d * q);
     return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc(), st_, &ws_);
   }
   int copyT(int k, const T *X, int64_t ldx, T *Y, int64_t ldy) {
@@ -496,6 +517,7 @@ int Engine<float>::use_tc() const { return 1; }
 template <typename T>
 void Engine<T>::free_all() {
   if (st_) cudaStreamSynchronize(st_);
+  if (store_shared_) store_ = nullptr;
   void *ptrs[] = {Sval32_, R032_, D32_,
                   V_[0], V_[1], store_, AW_,   R0_,  BWb_,    TMP_,    TMP2_,  AXc_,  BXc_,
                   Sval_, Abar_, Asave_, Qe_,   ph_,  t1_,     t2_,     theta_, lam_,  a0_,
@@ -538,7 +560,13 @@ int Engine<T>::setup(int size_x, int nev, int store_cap, int bs) {
   const size_t n = (size_t)n_;
   GCGE_CHECK(alloc_dev((void **)&V_[0], ts * n * ldV_));
   GCGE_CHECK(alloc_dev((void **)&V_[1], ts * n * ldV_));
-  GCGE_CHECK(alloc_dev((void **)&store_, ts * n * ldS_));
+  if (sizeof(T) == 8 && share_store && h_->store && h_->ld_store == ldS_ &&
+      h_->store_cap >= store_cap_) {
+    store_ = reinterpret_cast<T *>(h_->store);   // the FP64 engine locks straight into it
+    store_shared_ = true;
+  } else {
+    GCGE_CHECK(alloc_dev((void **)&store_, ts * n * ldS_));
+  }
   GCGE_CHECK(alloc_dev((void **)&AW_, ts * n * ldAW_));
   GCGE_CHECK(alloc_dev((void **)&R0_, ts * n * ldB_));
   GCGE_CHECK(alloc_dev((void **)&BWb_, ts * n * ldW_));
@@ -1313,7 +1341,7 @@ void add_stats(gcge_handle *h, const Engine<T> &e) {
 template <typename T>
 int export_store(gcge_handle *h, const Engine<T> &e) {
   const int k = std::min(e.nlock(), h->store_cap);
-  if (k > 0)
+  if (k > 0 && (const void *)e.store() != (const void *)h->store)
     GCGE_CHECK(copy_cols<T, double>(h->n, k, e.store(), e.ld_store(), h->store, h->ld_store,
                                     nullptr, h->st));
   h->lam.assign(e.locked_lam().begin(), e.locked_lam().begin() + k);
@@ -1327,6 +1355,7 @@ int export_store(gcge_handle *h, const Engine<T> &e) {
 int run_fp64(gcge_handle *h, const double *X0d, int64_t ld0, int *iters) {
   Engine<double> e(h, h->tol, h->opt.max_iter);
   e.checks = h->opt.checks != 0;
+  e.share_store = true;
   KProf prof;
   prof.st = h->st;
   if (h->opt.profile) e.prof = &prof;
@@ -1335,6 +1364,9 @@ int run_fp64(gcge_handle *h, const double *X0d, int64_t ld0, int *iters) {
   *iters = e.iterations();
   add_stats(h, e);
   if (s != GCGE_OK && s != GCGE_ENOTCONV) return s;
+  int tc_err = 0;   // a tensor-core kernel whose bounded wait ran out leaves a flag
+  GCGE_CHECK(tc_error_flag(&tc_err, h->st));
+  if (tc_err) return GCGE_ETIMEOUT;
   GCGE_CHECK(export_store(h, e));
   return s;
 }
@@ -1399,6 +1431,7 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     e2.use_p = h->moving || !p1_all;
     if (h->opt.profile) e2.prof = &prof;
     e2.reservoir_planned = true;
+    e2.share_store = true;
     s = e2.setup(sx, h->nev, h->store_cap, bs2);
     if (s == GCGE_OK) {
       e2.set_reservoir(Z, ldz, nz);
@@ -1406,6 +1439,12 @@ int run_mixed(gcge_handle *h, const double *X0d, int64_t ld0, int *iters, int *i
     }
     *iters = it1 + e2.iterations();
     add_stats(h, e2);
+    if (s == GCGE_OK || s == GCGE_ENOTCONV) {
+      int tc_err = 0;
+      const int s3 = tc_error_flag(&tc_err, h->st);
+      if (s3 != GCGE_OK) s = s3;
+      else if (tc_err) s = GCGE_ETIMEOUT;
+    }
     if (s == GCGE_OK || s == GCGE_ENOTCONV) {
       const int s2 = export_store(h, e2);
       if (s2 != GCGE_OK) s = s2;
