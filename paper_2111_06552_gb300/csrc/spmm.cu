@@ -11,10 +11,11 @@
 // a whole row's worth of FMAs and keeps many independent gathers in flight; the
 // nonzero loop is unrolled by four.
 //
-// Each CTA walks one contiguous block of rows, 256 / G rows at a time, with two to four
-// CTAs per SM: consecutive rows of a banded (stencil / FEM) matrix gather mostly the same
-// rows of X, which then stay in L1 between the CTA's steps instead of being fetched
-// from L2 once per nonzero.
+// The rows are dealt to the CTAs in chunks of 8 CTA steps (256 / G rows per step), in
+// turn, two to four CTAs per SM: within a chunk consecutive rows of a banded (stencil /
+// FEM) matrix gather mostly the same rows of X, which stay in L1 between the CTA's
+// steps; across the grid all CTAs sweep the rows together, so the rows of X that are
+// gathered again a grid plane later (3D stencils) are still in L2.
 //
 // Optional fused epilogue (used by the CG step): per column j the dot product
 // sum_i X[i, j] (A X)[i, j].  Each thread accumulates its own rows in the block's
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kSpmmThreads)
 spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
             const T *__restrict__ val, int k, int G, T alpha, const T *__restrict__ X,
             int64_t ldx, T beta, T *__restrict__ Y, int64_t ldy, double *__restrict__ part,
-            double *__restrict__ dot_out, unsigned *__restrict__ ticket, int64_t rows_per_cta) {
+            double *__restrict__ dot_out, unsigned *__restrict__ ticket, int64_t chunk_rows) {
   extern __shared__ double sdot[];   // per-warp column sums (warps x k), then blockDim.x scratch
   const int nchunks = (k + VEC - 1) / VEC;
   const int full = k / VEC;                 // chunks that are complete
@@ -74,9 +75,13 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
 #pragma unroll
     for (int v = 0; v < VEC; ++v) dacc[c][v] = T(0);
   const int64_t rows_per_step = blockDim.x / G;
-  const int64_t blk_end = min(n, (int64_t)(blockIdx.x + 1) * rows_per_cta);
-  for (int64_t row = (int64_t)blockIdx.x * rows_per_cta + threadIdx.x / G;
-       row - (threadIdx.x / G) < blk_end; row += rows_per_step) {
+  // chunks of consecutive rows dealt to the CTAs in turn: the whole grid sweeps the rows
+  // together, so the rows of X that a row's neighbours (in a 3D stencil, up to a grid
+  // plane away) gather again are still in L2 when they do
+  for (int64_t c0 = (int64_t)blockIdx.x * chunk_rows; c0 < n; c0 += (int64_t)gridDim.x * chunk_rows) {
+  const int64_t blk_end = min(n, c0 + chunk_rows);
+  for (int64_t row = c0 + threadIdx.x / G; row - (threadIdx.x / G) < blk_end;
+       row += rows_per_step) {
     T acc[NV][VEC];
 #pragma unroll
     for (int c = 0; c < NV; ++c)
@@ -184,6 +189,7 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
       }
     }
   }
+  }
   if (DOT) {
     // reduce over the warp's row groups (fixed butterfly order), one slot per warp
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -210,7 +216,7 @@ spmm_kernel(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
 
 struct Plan {
   int vec, G, nv, grid;
-  int64_t rows_per_cta;
+  int64_t chunk_rows;
 };
 
 template <typename T>
@@ -219,22 +225,27 @@ Plan plan_for(int64_t n, int k, bool aligned) {
   const int chunks = (k + vec - 1) / vec;
   int G = 1;
   // FP32 blocks up to 32 columns: at most two 16-byte chunks per lane (short register
-  // footprint, four CTAs per SM); otherwise up to eight chunks per lane, two CTAs per SM
+  // footprint, four CTAs per SM).  Wider FP32 blocks: one chunk per lane, so a warp (or
+  // a part of one) covers a whole row: each gather is one coalesced request of the
+  // row's bytes, and the warps of a CTA walk consecutive rows, whose neighbour rows of
+  // X they share in L1.  FP64 blocks: up to eight chunks per lane, two CTAs per SM (the
+  // FP64 pipe is the bound).
   const bool narrow = sizeof(T) == 4 && k <= 32;
-  const int cpl = narrow ? 2 : 8;
+  const bool wide32 = sizeof(T) == 4 && !narrow;
+  const int cpl = narrow ? 2 : (wide32 ? 1 : 8);
   while ((chunks + G - 1) / G > cpl && G < 32) G <<= 1;
   int nv = (chunks + G - 1) / G;
   if (nv > 8) nv = 8;           // k > 32 * 8 * vec: the caller splits the columns
   const int64_t step = kSpmmThreads / G;   // rows per CTA step
   int64_t grid = (n + step - 1) / step;
-  const int64_t cap = (int64_t)device_sm_count() * (narrow ? 4 : 2);   // row streams per SM
+  const int64_t cap = (int64_t)device_sm_count() * (sizeof(T) == 4 ? 4 : 2);   // row streams per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  int64_t rpc = (n + grid - 1) / grid;
-  rpc = ((rpc + step - 1) / step) * step;
-  grid = (n + rpc - 1) / rpc;
+  const int64_t chunk = step * 8;   // rows per chunk: 8 CTA steps
+  const int64_t nchunk = (n + chunk - 1) / chunk;
+  if (grid > nchunk) grid = nchunk;
   if (grid < 1) grid = 1;
-  return {vec, G, nv, (int)grid, rpc};
+  return {vec, G, nv, (int)grid, chunk};
 }
 
 template <typename T, int VEC, int NV>
@@ -243,8 +254,10 @@ void launch_v(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, c
               double *dot_out, unsigned *ticket, cudaStream_t st) {
   static bool carveout = false;   // X rows are re-read through L1: prefer L1 over shared
   if (!carveout) {
+    // the fused-dot variant keeps k doubles per warp in shared memory: leave room for
+    // four CTAs per SM (a zero carveout held it to one)
     cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, true>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 25);
     // the fused dot keeps one k-wide slot per warp (k <= 1024: 66 KB)
     cudaFuncSetAttribute(spmm_kernel<T, VEC, NV, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -256,11 +269,11 @@ void launch_v(const Plan &pl, int64_t n, const int32_t *rp, const int32_t *ci, c
   if (dot_out)
     spmm_kernel<T, VEC, NV, true><<<pl.grid, kSpmmThreads,
                                     (k * (kSpmmThreads / 32) + kSpmmThreads) * sizeof(double), st>>>(
-        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, pl.rows_per_cta);
+        n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, part, dot_out, ticket, pl.chunk_rows);
   else
     spmm_kernel<T, VEC, NV, false><<<pl.grid, kSpmmThreads, 0, st>>>(
         n, rp, ci, val, k, pl.G, alpha, X, ldx, beta, Y, ldy, nullptr, nullptr, nullptr,
-        pl.rows_per_cta);
+        pl.chunk_rows);
 }
 
 template <typename T, int VEC>
