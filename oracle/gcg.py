@@ -58,6 +58,7 @@ class Params:
     size_x: int | None = None
     orth: OrthParams = field(default_factory=OrthParams)
     orth_alg: int = 3            # STEP 2 by Algorithm 3 (default) or Algorithm 2
+    precond: bool = False        # STEP 6 by Jacobi-preconditioned CG (oracle/cg.py)
     # optional observer called with a dict at STEP 5 and STEP 6 (tests read the
     # iteration's intermediate blocks through it; it never changes the iteration)
     trace: object = None
@@ -190,7 +191,8 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
         Xn = X[:, lw:lw + bs_new]
         if p.trace is not None:
             p.trace(dict(step=6, it=it, Xn=Xn))
-        Wt, cg_it, _ = shifted_cg(A, B, theta, Xn, lam[lw:lw + bs_new], p.cg_max_iter, p.cg_rtol)
+        Wt, cg_it, _ = shifted_cg(A, B, theta, Xn, lam[lw:lw + bs_new], p.cg_max_iter, p.cg_rtol,
+                                  precond=p.precond)
         history[-1].update(theta=theta, cg_iters=int(cg_it.max()) if cg_it.size else 0)
         # ---- STEP 2: B-orthogonalise W against [X_c (store), X, P], then Algorithm 3
         Q0 = np.hstack([store, X, P])

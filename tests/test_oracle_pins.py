@@ -13,6 +13,7 @@ import os
 import numpy as np
 import pytest
 import scipy.linalg as sl
+import scipy.sparse as sp
 
 import workloads as W
 from oracle import linalg as L
@@ -112,6 +113,92 @@ def test_cg_stopping_rule_and_breakdown():
     _, it2, broke2 = CG.shifted_cg(A, None, 0.5 * (ev[0] + ev[1]), x + 0.0, np.array([0.0]),
                                    max_iter=30, rtol=0.0)
     assert broke2[0] and it2[0] == 0
+
+
+def _pcg_residuals(S, b, steps):
+    """Residuals r_j = b - S x_j of Jacobi-preconditioned CG after j = 0..steps steps."""
+    n = S.shape[0]
+    out = []
+    for j in range(steps + 1):
+        x, it, _ = CG.shifted_cg(S, None, 0.0, np.zeros((n, 1)), np.zeros(1), max_iter=j,
+                                 rtol=0.0, rhs=b[:, None], precond=True)
+        out.append(b - S @ x[:, 0])
+    return out
+
+
+def test_pcg_residuals_are_m_orthogonal():
+    """Preconditioned CG: r_i^T M^-1 r_j = 0 for i != j (textbook property), on the
+    lognormal FD operator whose diagonal varies over orders of magnitude."""
+    p = W.make_config("fd3d_128", N=8, seed=2)
+    S = p.A
+    b = np.random.default_rng(3).standard_normal(S.shape[0])
+    R = np.column_stack(_pcg_residuals(S, b, 8))
+    minv = CG.jacobi_inverse(S)
+    G = R.T @ (R * minv[:, None])
+    off = G - np.diag(np.diag(G))
+    assert np.abs(off).max() <= 1e-9 * np.sqrt(np.outer(np.diag(G), np.diag(G))).max()
+
+
+def test_pcg_diagonal_system_in_one_step():
+    """A diagonal S is its own Jacobi preconditioner: one step solves it exactly."""
+    d = np.linspace(0.5, 300.0, 40)
+    S = sp.diags(d).tocsr()
+    b = np.random.default_rng(4).standard_normal(40)
+    x, it, _ = CG.shifted_cg(S, None, 0.0, np.zeros((40, 1)), np.zeros(1), max_iter=1,
+                             rtol=0.0, rhs=b[:, None], precond=True)
+    assert np.abs(x[:, 0] - b / d).max() <= 1e-14 * np.abs(b / d).max()
+
+
+def test_pcg_fewer_steps_on_high_contrast_operator():
+    p = W.make_config("fd3d_128", N=12, seed=1)
+    S = p.A
+    b = np.random.default_rng(5).standard_normal((S.shape[0], 2))
+    _, it_cg, _ = CG.shifted_cg(S, None, 0.0, np.zeros_like(b), np.zeros(2), max_iter=500,
+                                rtol=1e-8, rhs=b)
+    _, it_pcg, _ = CG.shifted_cg(S, None, 0.0, np.zeros_like(b), np.zeros(2), max_iter=500,
+                                 rtol=1e-8, rhs=b, precond=True)
+    assert it_pcg.max() < 0.7 * it_cg.max()
+
+
+def test_gcg_with_jacobi_pcg_closed_form():
+    p = W.make_config("q1_64", N=7)
+    nev, bs = 12, 3
+    r = G.gcg(p.A, p.B, nev, bs, 1e-8, W.initial_block(p.n, nev + 3 * bs, 1),
+              G.Params(precond=True))
+    exact = W.q1_eigs(7, nev)
+    assert r.converged
+    assert np.abs(r.evals - exact).max() <= 1e-8 * exact[0]
+
+
+def test_planted_pcg_unpreconditioned_beta_is_caught(monkeypatch):
+    # beta from r^T r instead of r^T M^-1 r breaks the M^-1-orthogonality of residuals
+    orig = CG.shifted_cg
+
+    def wrong(A, B, theta, X, lam, max_iter=30, rtol=1e-2, rhs=None, precond=False):
+        n, k = X.shape
+        S = CG.shifted_matrix(A, B, theta)
+        minv = CG.jacobi_inverse(S)[:, None]
+        x = X.copy()
+        r = rhs - S @ x
+        z = r * minv
+        p_ = z.copy()
+        rr = np.einsum("ij,ij->j", r, r)
+        rz = np.einsum("ij,ij->j", r, z)
+        for _ in range(max_iter):
+            q = S @ p_
+            alpha = rz / np.einsum("ij,ij->j", p_, q)
+            x += p_ * alpha
+            r -= q * alpha
+            z = r * minv
+            rr_new = np.einsum("ij,ij->j", r, r)
+            p_ = z + p_ * (rr_new / rr)
+            rr = rr_new
+            rz = np.einsum("ij,ij->j", r, z)
+        return x, np.full(k, max_iter), np.zeros(k, dtype=bool)
+
+    monkeypatch.setattr(CG, "shifted_cg", wrong)
+    with pytest.raises(AssertionError):
+        test_pcg_residuals_are_m_orthogonal()
 
 
 # ---------------------------------------------------------------- Algorithm 3 / 2 (STEP 2)
