@@ -88,6 +88,9 @@ typedef struct {
   int orth;                 /* STEP 2 orthogonaliser: GCGE_ORTH_ALG3 (RecursiveOrthSVD,
                                Algorithm 3) or GCGE_ORTH_ALG2 (modified block
                                orthogonalisation, Algorithm 2), Section 3.1        (ALG3) */
+  int precond;              /* STEP 6 preconditioner (Section 2 suggests one):
+                               GCGE_PRECOND_NONE or GCGE_PRECOND_JACOBI, M = |diag(A -
+                               theta B)| of the shifted system, same shift       (NONE)  */
   int fp64_emulation;       /* 1: large FP64 Gram and V C products run on the bf16 tensor
                                cores from exact digit slices (gcge_gram_f64_tc); 0: the
                                FP64 kernels only                                       (1)   */
@@ -96,6 +99,9 @@ typedef struct {
                                max_proj_dim - 2 blockSize columns. 0: 5 blockSize.
                                Must be >= 3 blockSize; ignored without moving.   (0)   */
 } gcge_options;
+
+#define GCGE_PRECOND_NONE 0
+#define GCGE_PRECOND_JACOBI 1
 
 #define GCGE_ORTH_ALG3 0      /* Algorithm 3: recursive halves, leaf M = W^T B W eigensolve */
 #define GCGE_ORTH_ALG2 1      /* Algorithm 2: blocks of b = min(m/4, 200) columns, modified
@@ -276,14 +282,18 @@ int gcge_syev(int d, double *d_A, int64_t lda, double *d_w, double *d_Q, int64_t
  * explicitly formed A - theta B), from the initial guess in d_X (n x k, ldx),
  * which is overwritten by the result; d_B is the n x k right-hand side (ldb).
  * Column j stops at ||r|| <= rtol ||r0||, after max_iter steps, or at a
- * breakdown p^T S p <= 0.  iters (host, k ints, may be NULL) receives the
- * steps taken per column.  Synchronises the stream. */
+ * breakdown p^T S p <= 0.  precond = GCGE_PRECOND_JACOBI runs preconditioned CG
+ * with M = |diag(S)| (Section 2 suggests preconditioning STEP 6); the stop test
+ * stays on the unpreconditioned ||r||.  iters (host, k ints, may be NULL)
+ * receives the steps taken per column.  Synchronises the stream. */
 int gcge_block_cg_f64(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col_idx,
                       const double *d_S, int k, const double *d_B, int64_t ldb, double *d_X,
-                      int64_t ldx, int max_iter, double rtol, int *iters, void *stream);
+                      int64_t ldx, int max_iter, double rtol, int precond, int *iters,
+                      void *stream);
 int gcge_block_cg_f32(int64_t n, const int32_t *d_row_ptr, const int32_t *d_col_idx,
                       const float *d_S, int k, const float *d_B, int64_t ldb, float *d_X,
-                      int64_t ldx, int max_iter, double rtol, int *iters, void *stream);
+                      int64_t ldx, int max_iter, double rtol, int precond, int *iters,
+                      void *stream);
 
 /* STEP 2 (Section 3.1): B-orthonormalise the n x m block d_W (row-major, ldw,
  * overwritten) against the B-orthonormal block d_Q (n x q, ldq; q may be 0), then

@@ -34,6 +34,8 @@ GCGE_ENAN = -7
 GCGE_ENOTREADY = -8
 GCGE_FP64 = 0
 GCGE_MIXED = 1
+GCGE_PRECOND_NONE = 0
+GCGE_PRECOND_JACOBI = 1
 GCGE_ORTH_ALG3 = 0
 GCGE_ORTH_ALG2 = 1
 KERNEL_CLASSES = ("spmm", "gram", "vc", "syev", "cgvec", "other", "spmm64", "gram64", "vc64",
@@ -59,8 +61,8 @@ class gcge_options(C.Structure):
                 ("size_x", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("initial_block", C.c_void_p), ("mixed_switch_tol", C.c_double),
                 ("verbose", C.c_int), ("checks", C.c_int), ("profile", C.c_int),
-                ("mixed_bs2", C.c_int), ("orth", C.c_int), ("fp64_emulation", C.c_int),
-                ("max_proj_dim", C.c_int)]
+                ("mixed_bs2", C.c_int), ("orth", C.c_int), ("precond", C.c_int),
+                ("fp64_emulation", C.c_int), ("max_proj_dim", C.c_int)]
 
 
 class gcge_stats(C.Structure):
@@ -97,8 +99,8 @@ _SIGS = {
     "gcge_vc_f64": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _P]),
     "gcge_vc_f32": (_I, [_I64, _I, _I, _D, _P, _I64, _P, _I64, _D, _P, _I64, _I, _P]),
     "gcge_syev": (_I, [_I, _P, _I64, _P, _P, _I64, C.POINTER(_I), _P]),
-    "gcge_block_cg_f64": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
-    "gcge_block_cg_f32": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _P, _P]),
+    "gcge_block_cg_f64": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _I, _P, _P]),
+    "gcge_block_cg_f32": (_I, [_I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _I, _D, _I, _P, _P]),
     "gcge_borth_f64": (_I, [_I64, _P, _P, _P, _P, _I64, _I, _P, _I64, _I, _I, _I, C.POINTER(_I),
                             _P]),
     "gcge_random_block_f64": (_I, [_I64, _I, C.c_uint64, _P, _I64, _P]),
@@ -211,18 +213,20 @@ def gcge_syev(d, A, lda, w, Q, ldq, stream=None):
     return sweeps.value
 
 
-def gcge_block_cg_f64(n, row_ptr, col_idx, S, k, Bm, ldb, X, ldx, max_iter, rtol, stream=None):
+def gcge_block_cg_f64(n, row_ptr, col_idx, S, k, Bm, ldb, X, ldx, max_iter, rtol, precond=0,
+                      stream=None):
     it = np.zeros(k, dtype=np.int32)
     _check(lib().gcge_block_cg_f64(n, _addr(row_ptr), _addr(col_idx), _addr(S), k, _addr(Bm), ldb,
-                                   _addr(X), ldx, max_iter, rtol, it.ctypes.data,
+                                   _addr(X), ldx, max_iter, rtol, precond, it.ctypes.data,
                                    _stream(stream)), "gcge_block_cg_f64")
     return it
 
 
-def gcge_block_cg_f32(n, row_ptr, col_idx, S, k, Bm, ldb, X, ldx, max_iter, rtol, stream=None):
+def gcge_block_cg_f32(n, row_ptr, col_idx, S, k, Bm, ldb, X, ldx, max_iter, rtol, precond=0,
+                      stream=None):
     it = np.zeros(k, dtype=np.int32)
     _check(lib().gcge_block_cg_f32(n, _addr(row_ptr), _addr(col_idx), _addr(S), k, _addr(Bm), ldb,
-                                   _addr(X), ldx, max_iter, rtol, it.ctypes.data,
+                                   _addr(X), ldx, max_iter, rtol, precond, it.ctypes.data,
                                    _stream(stream)), "gcge_block_cg_f32")
     return it
 

@@ -196,13 +196,25 @@ int gcge_syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, 
 
 int gcge_block_cg_f64(int64_t n, const int32_t *rp, const int32_t *ci, const double *S, int k,
                       const double *B, int64_t ldb, double *X, int64_t ldx, int max_iter,
-                      double rtol, int *iters, void *stream) {
+                      double rtol, int precond, int *iters, void *stream) {
   if (n < 1 || k < 1 || ldb < k || ldx < k || max_iter < 0) return GCGE_EINVAL;
+  if (precond != GCGE_PRECOND_NONE && precond != GCGE_PRECOND_JACOBI) return GCGE_EINVAL;
   if (bad_ptr(rp) || bad_ptr(ci) || bad_ptr(S) || bad_ptr(B) || bad_ptr(X)) return GCGE_EINVAL;
   CgWork<double> w;
   int64_t nl = 0;
+  cudaStream_t st = as_stream(stream);
+  double *minv = nullptr;
+  if (precond == GCGE_PRECOND_JACOBI) {
+    GCGE_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&minv), sizeof(double) * (size_t)n, st));
+    const int sj = jacobi_inverse<double>(n, rp, ci, S, minv, st);
+    if (sj != GCGE_OK) {
+      cudaFreeAsync(minv, st);
+      return sj;
+    }
+  }
   int s = block_cg<double>(n, rp, ci, S, k, B, ldb, nullptr, 0, X, ldx, max_iter, rtol, w, iters,
-                           &nl, as_stream(stream));
+                        &nl, st, nullptr, minv);
+  if (minv) cudaFreeAsync(minv, st);
   g_launches += nl;
   cudaStreamSynchronize(as_stream(stream));
   w.free_all();
@@ -211,13 +223,25 @@ int gcge_block_cg_f64(int64_t n, const int32_t *rp, const int32_t *ci, const dou
 
 int gcge_block_cg_f32(int64_t n, const int32_t *rp, const int32_t *ci, const float *S, int k,
                       const float *B, int64_t ldb, float *X, int64_t ldx, int max_iter,
-                      double rtol, int *iters, void *stream) {
+                      double rtol, int precond, int *iters, void *stream) {
   if (n < 1 || k < 1 || ldb < k || ldx < k || max_iter < 0) return GCGE_EINVAL;
+  if (precond != GCGE_PRECOND_NONE && precond != GCGE_PRECOND_JACOBI) return GCGE_EINVAL;
   if (bad_ptr(rp) || bad_ptr(ci) || bad_ptr(S) || bad_ptr(B) || bad_ptr(X)) return GCGE_EINVAL;
   CgWork<float> w;
   int64_t nl = 0;
+  cudaStream_t st = as_stream(stream);
+  float *minv = nullptr;
+  if (precond == GCGE_PRECOND_JACOBI) {
+    GCGE_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&minv), sizeof(float) * (size_t)n, st));
+    const int sj = jacobi_inverse<float>(n, rp, ci, S, minv, st);
+    if (sj != GCGE_OK) {
+      cudaFreeAsync(minv, st);
+      return sj;
+    }
+  }
   int s = block_cg<float>(n, rp, ci, S, k, B, ldb, nullptr, 0, X, ldx, max_iter, rtol, w, iters,
-                          &nl, as_stream(stream));
+                        &nl, st, nullptr, minv);
+  if (minv) cudaFreeAsync(minv, st);
   g_launches += nl;
   cudaStreamSynchronize(as_stream(stream));
   w.free_all();

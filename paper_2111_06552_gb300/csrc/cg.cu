@@ -8,6 +8,9 @@
 //      (last CTA: rr_new[k], and the breakdown flags for p^T S p <= 0);
 //   3. beta_j = rr_new_j / rr_j; p = r + beta p (last CTA commits rr, the step
 //      counts and the stop flags ||r|| <= rtol ||r0||).
+// With a Jacobi preconditioner M^-1 = 1 / |diag(S)| (per row) the same three kernels
+// run preconditioned CG: z = M^-1 r is formed on the fly where it is read, alpha and
+// beta use r^T z, and the stop test stays on the unpreconditioned ||r||.
 // Vector kernels move 16-byte chunks when the blocks are aligned.  A stopped
 // column takes no further updates.  Breakdown: S = A - theta B is only SPD on the
 // complement of the locked vectors (Section 3.2), so p^T S p <= 0 stops a column.
@@ -39,7 +42,8 @@ struct Slice {
 // the inexact inner CG); the block and cross-CTA sums run in FP64, in a fixed order.
 template <int VEC, typename A>
 __device__ __forceinline__ void block_cols_to_part(const Slice<VEC> &sl, int k, const A (&acc)[VEC],
-                                                   double *sred, double *part) {
+                                                   double *sred, double *part, int pstride,
+                                                   int poff) {
   // sred: kCgThreads * VEC doubles laid out [row0][chunk*VEC + v] with row stride chunks*VEC
   const int w = sl.chunks * VEC;
   if (sl.on)
@@ -49,7 +53,7 @@ __device__ __forceinline__ void block_cols_to_part(const Slice<VEC> &sl, int k, 
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double s = 0.0;
     for (int r = 0; r < sl.rows_per_block; ++r) s += sred[r * w + j];
-    part[(int64_t)blockIdx.x * k + j] = s;
+    part[(int64_t)blockIdx.x * pstride + poff + j] = s;
   }
 }
 
@@ -77,67 +81,85 @@ __device__ __forceinline__ void st_vec(T *p, const T (&v)[VEC]) {
   }
 }
 
-// rr_j = sum r_j^2 (initial): last CTA writes rr, r0, active, iters, broke.
+// Initial sums: rr_j = r_j^T r_j, rz_j = r_j^T M^-1 r_j, and p = M^-1 r; the last CTA
+// writes rr, rz, r0, active, iters, broke.
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kCgThreads)
-cg_init_kernel(int64_t n, int k, const T *__restrict__ r, int64_t ld, double *__restrict__ part,
-               unsigned *__restrict__ ticket, double *__restrict__ rr, double *__restrict__ r0,
-               int *__restrict__ active, int *__restrict__ iters, int *__restrict__ broke,
-               double rtol) {
+cg_init_kernel(int64_t n, int k, const T *__restrict__ r, T *__restrict__ p, int64_t ld,
+               const T *__restrict__ minv, double *__restrict__ part,
+               unsigned *__restrict__ ticket, double *__restrict__ rr, double *__restrict__ rz,
+               double *__restrict__ r0, int *__restrict__ active, int *__restrict__ iters,
+               int *__restrict__ broke, double rtol) {
   extern __shared__ double sm[];
   Slice<VEC> sl(k);
-  T acc[VEC];
+  T acc[VEC], accz[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+  for (int v = 0; v < VEC; ++v) acc[v] = accz[v] = T(0);
   if (sl.on) {
     for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
          row += (int64_t)gridDim.x * sl.rows_per_block) {
       const int j0 = sl.chunk * VEC;
+      const T mi = minv ? minv[row] : T(1);
       if (j0 + VEC <= k) {
-        T rv[VEC];
+        T rv[VEC], zv[VEC];
         ld_vec<T, VEC>(r + row * ld + j0, rv);
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[v] += rv[v] * rv[v];
+        for (int v = 0; v < VEC; ++v) {
+          zv[v] = mi * rv[v];
+          acc[v] += rv[v] * rv[v];
+          accz[v] += rv[v] * zv[v];
+        }
+        st_vec<T, VEC>(p + row * ld + j0, zv);
       } else {
         for (int v = 0; v < VEC && j0 + v < k; ++v) {
-          const T x = r[row * ld + j0 + v];
+          const T x = r[row * ld + j0 + v], z = mi * x;
+          p[row * ld + j0 + v] = z;
           acc[v] += x * x;
+          accz[v] += x * z;
         }
       }
     }
   }
-  block_cols_to_part<VEC>(sl, k, acc, sm, part);
+  block_cols_to_part<VEC>(sl, k, acc, sm, part, 2 * k, 0);
   __syncthreads();
-  last_cta_reduce(k, part, ticket, sm, [&](int j, double s) {
-    rr[j] = s;
-    const double nr = sqrt(s);
-    r0[j] = nr;
-    active[j] = (nr <= rtol * nr) ? 0 : 1;
-    iters[j] = 0;
-    broke[j] = 0;
+  block_cols_to_part<VEC>(sl, k, accz, sm, part, 2 * k, k);
+  __syncthreads();
+  last_cta_reduce(2 * k, part, ticket, sm, [&](int j, double s) {
+    if (j < k) {
+      rr[j] = s;
+      const double nr = sqrt(s);
+      r0[j] = nr;
+      active[j] = (nr <= rtol * nr) ? 0 : 1;
+      iters[j] = 0;
+      broke[j] = 0;
+    } else {
+      rz[j - k] = s;
+    }
   });
 }
 
-// x += alpha p, r -= alpha q; partial r^T r; last CTA: rrn and breakdown flags.
+// alpha = rz / pq; x += alpha p, r -= alpha q; partial r^T r and r^T M^-1 r; last CTA:
+// rrn, rzn and the breakdown flags.
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kCgThreads)
-cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *__restrict__ rr,
+cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *__restrict__ rz,
                  int *__restrict__ active, int *__restrict__ broke, T *__restrict__ x,
                  int64_t ldx, const T *__restrict__ p, T *__restrict__ r,
-                 const T *__restrict__ q, int64_t ld, double *__restrict__ part,
-                 unsigned *__restrict__ ticket, double *__restrict__ rrn) {
+                 const T *__restrict__ q, int64_t ld, const T *__restrict__ minv,
+                 double *__restrict__ part, unsigned *__restrict__ ticket,
+                 double *__restrict__ rrn, double *__restrict__ rzn) {
   extern __shared__ double sm[];
   double *salpha = sm;                       // k
   double *sred = sm + k;                     // kCgThreads * VEC
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const bool a = active[j] && pq[j] > 0.0;
-    salpha[j] = a ? rr[j] / pq[j] : 0.0;
+    salpha[j] = a ? rz[j] / pq[j] : 0.0;
   }
   __syncthreads();
   Slice<VEC> sl(k);
-  T acc[VEC];
+  T acc[VEC], accz[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = T(0);
+  for (int v = 0; v < VEC; ++v) acc[v] = accz[v] = T(0);
   if (sl.on) {
     const int j0 = sl.chunk * VEC;
     T al[VEC];
@@ -146,6 +168,7 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
     const bool full = j0 + VEC <= k;
     for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
          row += (int64_t)gridDim.x * sl.rows_per_block) {
+      const T mi = minv ? minv[row] : T(1);
       if (full) {
         T xv[VEC], pv[VEC], rv[VEC], qv[VEC];
         ld_vec<T, VEC>(x + row * ldx + j0, xv);
@@ -157,6 +180,7 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
           xv[v] += al[v] * pv[v];
           rv[v] -= al[v] * qv[v];
           acc[v] += rv[v] * rv[v];
+          accz[v] += rv[v] * (mi * rv[v]);
         }
         st_vec<T, VEC>(x + row * ldx + j0, xv);
         st_vec<T, VEC>(r + row * ld + j0, rv);
@@ -167,35 +191,44 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
           const T rv = r[row * ld + j] - al[v] * q[row * ld + j];
           r[row * ld + j] = rv;
           acc[v] += rv * rv;
+          accz[v] += rv * (mi * rv);
         }
       }
     }
   }
-  block_cols_to_part<VEC>(sl, k, acc, sred, part);
+  block_cols_to_part<VEC>(sl, k, acc, sred, part, 2 * k, 0);
   __syncthreads();
-  last_cta_reduce(k, part, ticket, sred, [&](int j, double s) {
-    rrn[j] = s;
-    if (active[j] && !(pq[j] > 0.0)) {
-      active[j] = 0;
-      broke[j] = 1;
+  block_cols_to_part<VEC>(sl, k, accz, sred, part, 2 * k, k);
+  __syncthreads();
+  last_cta_reduce(2 * k, part, ticket, sred, [&](int j, double s) {
+    if (j < k) {
+      rrn[j] = s;
+      if (active[j] && !(pq[j] > 0.0)) {
+        active[j] = 0;
+        broke[j] = 1;
+      }
+    } else {
+      rzn[j - k] = s;
     }
   });
 }
 
-// p = r + beta p for active columns; last CTA commits rr = rrn, iters, stop flags.
+// beta = rzn / rz; p = M^-1 r + beta p for active columns; the last CTA commits rr = rrn,
+// rz = rzn, the step counts and the stop flags (||r|| <= rtol ||r0||).
 template <typename T, int VEC>
 __global__ void __launch_bounds__(kCgThreads)
 cg_pupdate_kernel(int64_t n, int k, const double *__restrict__ rrn, double *__restrict__ rr,
+                  const double *__restrict__ rzn, double *__restrict__ rz,
                   const double *__restrict__ r0, int *__restrict__ active,
                   int *__restrict__ iters, T *__restrict__ p, const T *__restrict__ r, int64_t ld,
-                  unsigned *__restrict__ ticket, double rtol) {
+                  const T *__restrict__ minv, unsigned *__restrict__ ticket, double rtol) {
   extern __shared__ double sm[];
   double *sbeta = sm;                        // k
   int *sact = (int *)(sm + k);               // k
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const int a = active[j];
     sact[j] = a;
-    sbeta[j] = a ? rrn[j] / rr[j] : 0.0;
+    sbeta[j] = a ? rzn[j] / rz[j] : 0.0;
   }
   __syncthreads();
   Slice<VEC> sl(k);
@@ -213,22 +246,24 @@ cg_pupdate_kernel(int64_t n, int k, const double *__restrict__ rrn, double *__re
     if (any) {
       for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
            row += (int64_t)gridDim.x * sl.rows_per_block) {
+        const T mi = minv ? minv[row] : T(1);
         if (full) {
           T pv[VEC], rv[VEC];
           ld_vec<T, VEC>(p + row * ld + j0, pv);
           ld_vec<T, VEC>(r + row * ld + j0, rv);
 #pragma unroll
           for (int v = 0; v < VEC; ++v)
-            if (sact[j0 + v]) pv[v] = rv[v] + be[v] * pv[v];
+            if (sact[j0 + v]) pv[v] = mi * rv[v] + be[v] * pv[v];
           st_vec<T, VEC>(p + row * ld + j0, pv);
         } else {
           for (int v = 0; v < VEC && j0 + v < k; ++v)
-            if (sact[j0 + v]) p[row * ld + j0 + v] = r[row * ld + j0 + v] + be[v] * p[row * ld + j0 + v];
+            if (sact[j0 + v])
+              p[row * ld + j0 + v] = mi * r[row * ld + j0 + v] + be[v] * p[row * ld + j0 + v];
         }
       }
     }
   }
-  // commit after every CTA has read rr: the last CTA to arrive does it
+  // commit after every CTA has read rz: the last CTA to arrive does it
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
@@ -239,10 +274,35 @@ cg_pupdate_kernel(int64_t n, int k, const double *__restrict__ rrn, double *__re
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     if (!active[j]) continue;
     rr[j] = rrn[j];
+    rz[j] = rzn[j];
     iters[j] += 1;
     if (sqrt(rrn[j]) <= rtol * r0[j]) active[j] = 0;
   }
   if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// minv[i] = 1 / |S_ii| from the sorted CSR row (binary search for column i).
+template <typename T>
+__global__ void jacobi_inverse_kernel(int64_t n, const int32_t *__restrict__ rp,
+                                      const int32_t *__restrict__ ci, const T *__restrict__ S,
+                                      T *__restrict__ minv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = rp[i], hi = rp[i + 1] - 1;
+    T d = T(0);
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int c = ci[mid];
+      if (c == (int)i) {
+        d = S[mid];
+        break;
+      }
+      if (c < (int)i) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    const T a = d < T(0) ? -d : d;
+    minv[i] = a > T(0) ? T(1) / a : T(1);
+  }
 }
 
 int upd_grid(int64_t n, int k) {
@@ -275,8 +335,8 @@ int CgWork<T>::alloc(int64_t n, int k) {
   GCGE_CUDA(cudaMalloc(&p, vb));
   GCGE_CUDA(cudaMalloc(&q, vb));
   GCGE_CUDA(cudaMalloc(&part_a, sizeof(double) * (size_t)nb * k));
-  GCGE_CUDA(cudaMalloc(&part_b, sizeof(double) * (size_t)nb * k));
-  GCGE_CUDA(cudaMalloc(&scal, sizeof(double) * 4 * (size_t)k));
+  GCGE_CUDA(cudaMalloc(&part_b, sizeof(double) * (size_t)nb * 2 * k));
+  GCGE_CUDA(cudaMalloc(&scal, sizeof(double) * 6 * (size_t)k));
   GCGE_CUDA(cudaMalloc(&flags, sizeof(int) * 3 * (size_t)k));
   GCGE_CUDA(cudaMalloc(&tickets, sizeof(unsigned) * 4));
   GCGE_CUDA(cudaMemset(tickets, 0, sizeof(unsigned) * 4));
@@ -285,6 +345,8 @@ int CgWork<T>::alloc(int64_t n, int k) {
   r0 = scal + k;
   pq = scal + 2 * k;
   rrn = scal + 3 * k;
+  rz = scal + 4 * k;
+  rzn = scal + 5 * k;
   active = flags;
   iters = flags + k;
   broke = flags + 2 * k;
@@ -300,7 +362,7 @@ void CgWork<T>::free_all() {
   cudaFree(scal); cudaFree(flags); cudaFree(tickets);
   if (h_active) cudaFreeHost(h_active);
   r = p = q = nullptr;
-  part_a = part_b = scal = rr = r0 = pq = rrn = nullptr;
+  part_a = part_b = scal = rr = r0 = pq = rrn = rz = rzn = nullptr;
   flags = active = iters = broke = h_active = nullptr;
   tickets = nullptr;
   ncap = 0;
@@ -310,21 +372,22 @@ void CgWork<T>::free_all() {
 template <typename T, int VEC>
 static int cg_loop(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
                    T *X, int64_t ldx, int max_iter, double rtol, CgWork<T> &w, int64_t &nl,
-                   cudaStream_t st, KProf *prof, double spmm_bytes, double nnzS) {
+                   cudaStream_t st, KProf *prof, double spmm_bytes, double nnzS,
+                   const T *minv) {
   const int64_t ld = w.ld;
   const int nbb = upd_grid(n, k);
   if (nbb > w.nbcap || k > w.kcap) return GCGE_EINVAL;
   const int chunks = (k + VEC - 1) / VEC;
-  const size_t sm_r = sizeof(double) * (size_t)kCgThreads * VEC + 64;
+  const size_t sm_r = sizeof(double) * (size_t)kCgThreads * VEC + 64;   // >= blockDim doubles
   const size_t sm_u = sizeof(double) * ((size_t)k + (size_t)kCgThreads * VEC) + 64;
   const size_t sm_p = (sizeof(double) + sizeof(int)) * (size_t)k + 64;
   (void)chunks;
   const double ts = sizeof(T), nk = (double)n * k;
   {
     ProfScope ps(prof, GCGE_K_CGVEC, nk * ts, 2.0 * nk);
-    cg_init_kernel<T, VEC><<<nbb, kCgThreads, sm_r, st>>>(n, k, w.r, ld, w.part_b, w.tickets + 1,
-                                                          w.rr, w.r0, w.active, w.iters, w.broke,
-                                                          rtol);
+    cg_init_kernel<T, VEC><<<nbb, kCgThreads, sm_r, st>>>(n, k, w.r, w.p, ld, minv, w.part_b,
+                                                          w.tickets + 1, w.rr, w.rz, w.r0,
+                                                          w.active, w.iters, w.broke, rtol);
     GCGE_LAUNCH_CHECK();
     ++nl;
   }
@@ -336,13 +399,14 @@ static int cg_loop(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, 
     }
     {
       ProfScope ps(prof, GCGE_K_CGVEC, 9.0 * nk * ts, 6.0 * nk);
-      cg_update_kernel<T, VEC><<<nbb, kCgThreads, sm_u, st>>>(n, k, w.pq, w.rr, w.active, w.broke,
-                                                              X, ldx, w.p, w.r, w.q, ld, w.part_b,
-                                                              w.tickets + 2, w.rrn);
+      cg_update_kernel<T, VEC><<<nbb, kCgThreads, sm_u, st>>>(n, k, w.pq, w.rz, w.active, w.broke,
+                                                              X, ldx, w.p, w.r, w.q, ld, minv,
+                                                              w.part_b, w.tickets + 2, w.rrn,
+                                                              w.rzn);
       GCGE_LAUNCH_CHECK();
-      cg_pupdate_kernel<T, VEC><<<nbb, kCgThreads, sm_p, st>>>(n, k, w.rrn, w.rr, w.r0, w.active,
-                                                               w.iters, w.p, w.r, ld,
-                                                               w.tickets + 3, rtol);
+      cg_pupdate_kernel<T, VEC><<<nbb, kCgThreads, sm_p, st>>>(n, k, w.rrn, w.rr, w.rzn, w.rz,
+                                                               w.r0, w.active, w.iters, w.p, w.r,
+                                                               ld, minv, w.tickets + 3, rtol);
       GCGE_LAUNCH_CHECK();
     }
     nl += 3;
@@ -362,7 +426,7 @@ template <typename T>
 int block_cg(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k, const T *B,
              int64_t ldb, const T *r_init, int64_t ldr, T *X, int64_t ldx, int max_iter,
              double rtol, CgWork<T> &w, int *iters_host, int64_t *launches, cudaStream_t st,
-             KProf *prof) {
+             KProf *prof, const T *minv) {
   if (k <= 0 || n <= 0) return GCGE_OK;
   GCGE_CHECK(w.alloc(n, k));
   const int64_t ld = w.ld;
@@ -379,15 +443,14 @@ int block_cg(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
     GCGE_CHECK(launch_spmm<T>(n, rp, ci, S, k, T(-1), X, ldx, T(1), w.r, ld, nullptr, 0, st));
     ++nl;
   }
-  GCGE_CHECK(copy_cols<T, T>(n, k, w.r, ld, w.p, ld, nullptr, st));
-  nl += 2;
+  nl += 1;   // p = M^-1 r is written by the first kernel of the loop
   constexpr int vmax = 16 / sizeof(T);
   if (cg_aligned<T>(X, ldx, w.r, ld))
     GCGE_CHECK(cg_loop<T, vmax>(n, rp, ci, S, k, X, ldx, max_iter, rtol, w, nl, st, prof,
-                                spmm_bytes, nnz_last));
+                                spmm_bytes, nnz_last, minv));
   else
     GCGE_CHECK(cg_loop<T, 1>(n, rp, ci, S, k, X, ldx, max_iter, rtol, w, nl, st, prof, spmm_bytes,
-                             nnz_last));
+                             nnz_last, minv));
   int mx = 0;
   if (iters_host) {
     GCGE_CUDA(cudaMemcpyAsync(iters_host, w.iters, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
@@ -398,15 +461,30 @@ int block_cg(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, int k,
   return mx;
 }
 
+template <typename T>
+int jacobi_inverse(int64_t n, const int32_t *rp, const int32_t *ci, const T *S, T *minv,
+                   cudaStream_t st) {
+  if (n <= 0) return GCGE_OK;
+  int64_t g = (n + 255) / 256;
+  if (g > 8 * (int64_t)device_sm_count()) g = 8 * (int64_t)device_sm_count();
+  jacobi_inverse_kernel<T><<<(int)g, 256, 0, st>>>(n, rp, ci, S, minv);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
+}
+
+template int jacobi_inverse<double>(int64_t, const int32_t *, const int32_t *, const double *,
+                                   double *, cudaStream_t);
+template int jacobi_inverse<float>(int64_t, const int32_t *, const int32_t *, const float *,
+                                  float *, cudaStream_t);
 template struct CgWork<double>;
 template struct CgWork<float>;
 template int block_cg<double>(int64_t, const int32_t *, const int32_t *, const double *, int,
                               const double *, int64_t, const double *, int64_t, double *, int64_t,
                               int, double, CgWork<double> &, int *, int64_t *, cudaStream_t,
-                              KProf *);
+                              KProf *, const double *);
 template int block_cg<float>(int64_t, const int32_t *, const int32_t *, const float *, int,
                              const float *, int64_t, const float *, int64_t, float *, int64_t,
                              int, double, CgWork<float> &, int *, int64_t *, cudaStream_t,
-                             KProf *);
+                             KProf *, const float *);
 
 }  // namespace gcge

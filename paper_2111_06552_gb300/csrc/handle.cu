@@ -416,6 +416,7 @@ int gcge_options_default(gcge_options *o) {
   o->checks = 0;
   o->profile = 0;
   o->orth = GCGE_ORTH_ALG3;
+  o->precond = GCGE_PRECOND_NONE;
   o->fp64_emulation = 1;
   o->max_proj_dim = 0;
   return GCGE_OK;
@@ -438,6 +439,7 @@ int gcge_create(const gcge_csr *A, const gcge_csr *B, int nev, int block_size, d
   if (h->opt.cg_max_iter < 0 || h->opt.orth_leaf < 1 || h->opt.max_iter < 1 ||
       h->opt.mixed_bs2 < 0 || h->opt.max_proj_dim < 0 ||
       (h->opt.orth != GCGE_ORTH_ALG3 && h->opt.orth != GCGE_ORTH_ALG2) ||
+      (h->opt.precond != GCGE_PRECOND_NONE && h->opt.precond != GCGE_PRECOND_JACOBI) ||
       (h->opt.precision != GCGE_FP64 && h->opt.precision != GCGE_MIXED)) {
     delete h;
     return GCGE_EINVAL;

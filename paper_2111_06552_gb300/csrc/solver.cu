@@ -389,6 +389,8 @@ class Engine {
   CgWork<T> cg_;
   CgWork<float> cg32_;
   float *Sval32_ = nullptr, *R032_ = nullptr, *D32_ = nullptr;   // FP32 inner-CG buffers
+  T *Minv_ = nullptr;              // Jacobi preconditioner 1 / |diag(S)| (option precond)
+  float *Minv32_ = nullptr;
   double theta32_cur_ = -1.0;
   // iteration state
   int off_ = 0, kx_ = 0, np_ = 0, nw_ = 0, nb_old_ = 0, lw_ = 0;
@@ -518,7 +520,7 @@ template <typename T>
 void Engine<T>::free_all() {
   if (st_) cudaStreamSynchronize(st_);
   if (store_shared_) store_ = nullptr;
-  void *ptrs[] = {Sval32_, R032_, D32_,
+  void *ptrs[] = {Sval32_, R032_, D32_, Minv_, Minv32_,
                   V_[0], V_[1], store_, AW_,   R0_,  BWb_,    TMP_,    TMP2_,  AXc_,  BXc_,
                   Sval_, Abar_, Asave_, Qe_,   ph_,  t1_,     t2_,     theta_, lam_,  a0_,
                   Rg_,   Ms_,   Ml_,    Mq_,   Mc_,  d_norm2_, d_scale_, d_res_, d_crit_,
@@ -530,6 +532,8 @@ void Engine<T>::free_all() {
   Ms_ = Ml_ = Mq_ = Mc_ = d_norm2_ = d_scale_ = d_res_ = d_crit_ = d_lamn_ = d_m1_ = nullptr;
   d_idx_ = d_cnt_ = nullptr;
   Sval32_ = R032_ = D32_ = nullptr;
+  Minv_ = nullptr;
+  Minv32_ = nullptr;
   cg32_.free_all();
   if (h_d_) cudaFreeHost(h_d_);
   if (h_i_) cudaFreeHost(h_i_);
@@ -602,6 +606,12 @@ int Engine<T>::setup(int size_x, int nev, int store_cap, int bs) {
   GCGE_CUDA(cudaMallocHost(&h_d_, sizeof(double) * (2 * ldC_ + 8)));
   GCGE_CUDA(cudaMallocHost(&h_i_, sizeof(int) * (ldB_ + 8)));
   GCGE_CHECK(sw_.alloc(std::max(dmax_, kLeaf)));
+  if (h_->opt.precond == GCGE_PRECOND_JACOBI) {
+    if (cg_fp32 && sizeof(T) == 8)
+      GCGE_CHECK(alloc_dev((void **)&Minv32_, sizeof(float) * n));
+    else
+      GCGE_CHECK(alloc_dev((void **)&Minv_, ts * n));
+  }
   if (cg_fp32 && sizeof(T) == 8) {
     GCGE_CHECK(alloc_dev((void **)&Sval32_, sizeof(float) * (size_t)h_->S.nnz));
     GCGE_CHECK(alloc_dev((void **)&R032_, sizeof(float) * n * ldB_));
@@ -1032,6 +1042,10 @@ int Engine<T>::shifted_cg(const T *Xn, int64_t ldx, int bsn, const T *AXn, int64
     g_launches += 1;
     GCGE_CHECK(shifted_values<T>(h_->S.nnz, h_->mapA, h_->A.v64, bI_ ? nullptr : h_->mapB,
                                  bI_ ? nullptr : h_->B.v64, h_->isdiag, theta, Sval_, st_));
+    if (Minv_) {
+      g_launches += 1;
+      GCGE_CHECK(jacobi_inverse<T>(n_, h_->S.rp, h_->S.ci, Sval_, Minv_, st_));
+    }
     theta_cur_ = theta;
   }
   // initial guess x = X_n; initial residual r0 = (lambda - theta) B x - S x = lambda B x - A x
@@ -1047,20 +1061,25 @@ int Engine<T>::shifted_cg(const T *Xn, int64_t ldx, int bsn, const T *AXn, int64
       GCGE_CHECK(shifted_values<float>(h_->S.nnz, h_->mapA, h_->A.v64, bI_ ? nullptr : h_->mapB,
                                        bI_ ? nullptr : h_->B.v64, h_->isdiag, theta, Sval32_,
                                        st_));
+      if (Minv32_) {
+        g_launches += 1;
+        GCGE_CHECK(jacobi_inverse<float>(n_, h_->S.rp, h_->S.ci, Sval32_, Minv32_, st_));
+      }
       theta32_cur_ = theta;
     }
     g_launches += 2;
     GCGE_CHECK(copy_cols<T, float>(n_, bsn, R0_, ldB_, R032_, ldB_, nullptr, st_));
     GCGE_CUDA(cudaMemsetAsync(D32_, 0, sizeof(float) * (size_t)n_ * ldB_, st_));
     mx = block_cg<float>(n_, h_->S.rp, h_->S.ci, Sval32_, bsn, nullptr, 0, R032_, ldB_, D32_,
-                         ldB_, h_->opt.cg_max_iter, h_->opt.cg_rtol, cg32_, h_i_, &nl, st_, prof);
+                         ldB_, h_->opt.cg_max_iter, h_->opt.cg_rtol, cg32_, h_i_, &nl, st_, prof,
+                         Minv32_);
     if (mx >= 0) {
       g_launches += 1;
       GCGE_CHECK(add_cols<float, T>(n_, bsn, D32_, ldB_, Wout, ldw, st_));
     }
   } else {
     mx = block_cg<T>(n_, h_->S.rp, h_->S.ci, Sval_, bsn, nullptr, 0, R0_, ldB_, Wout, ldw,
-                     h_->opt.cg_max_iter, h_->opt.cg_rtol, cg_, h_i_, &nl, st_, prof);
+                     h_->opt.cg_max_iter, h_->opt.cg_rtol, cg_, h_i_, &nl, st_, prof, Minv_);
   }
   g_launches += nl;
   if (mx < 0) return mx;
@@ -1102,6 +1121,7 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
   lam_lock_.clear();
   bool first = true;
   int since_lock = 0;            // iterations without a new lock and without progress
+  int no_lock = 0;               // iterations without a new lock at all
   double best_res = 1e300;       // best residual of the first unconverged column
   double prev_lam = 1e300;       // its Ritz value in the previous iteration
   while (true) {
@@ -1141,9 +1161,11 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
       for (int j = 0; j < c; ++j) lam_lock_.push_back(lam_h_[j]);
       nlock_ += c;
       since_lock = 0;
+      no_lock = 0;
       best_res = 1e300;
       prev_lam = 1e300;
     } else {
+      ++no_lock;
       // progress: the residual of the first unconverged column gains 10% on its best, or
       // its Ritz value still falls (the start block is far from the eigenvector)
       const double lam_first = (size_t)c < lam_h_.size() ? lam_h_[c] : 0.0;
@@ -1160,11 +1182,14 @@ int Engine<T>::run(const double *X0d, int64_t ld0, const float *X0f, int64_t ld0
     if (h_->opt.verbose)
       fprintf(stderr, "[gcge] it %4d d %4d nconv %5d first-unlocked %.12e theta %.6e%s\n", it_, d,
               nlock_, (size_t)c < lam_h_.size() ? lam_h_[c] : 0.0, theta_cur_, move ? " move" : "");
-    const bool stop = nlock_ >= nev_ || it_ >= max_iter_ ||
-                      (stagnation_limit > 0 && since_lock >= stagnation_limit);
+    // FP32 rounding can keep a Ritz value drifting below the eigenvalue, which reads as
+    // progress: the phase also ends after 4 x stagnation_limit iterations without a lock
+    const bool stalled = stagnation_limit > 0 &&
+                         (since_lock >= stagnation_limit || no_lock >= 4 * stagnation_limit);
+    const bool stop = nlock_ >= nev_ || it_ >= max_iter_ || stalled;
     if (stop) {
       done_ = nlock_ >= nev_;
-      stagnated = !done_ && stagnation_limit > 0 && since_lock >= stagnation_limit;
+      stagnated = !done_ && stalled;
       cur_ = nxt;
       off_ = c;
       kx_ -= c;

@@ -208,6 +208,31 @@ def test_block_cg_matches_oracle(g, theta):
         assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("theta", [0.0, 0.7])
+def test_block_pcg_matches_oracle(g, theta):
+    """Jacobi-preconditioned CG (M = |diag(S)|) on the lognormal FD pencil: identical
+    per-column step counts and iterates to 1e-10 of the oracle's preconditioned CG."""
+    import torch
+    p = W.make_config("fd3d_128", N=10, seed=4)
+    n = p.n
+    k = 6
+    X0 = np.random.default_rng(5).standard_normal((n, k))
+    lam = np.linspace(20, 40, k)
+    rhs = L.spmm(p.B, X0) * (lam - theta)
+    S = CG.shifted_matrix(p.A, p.B, theta)
+    for max_iter, rtol in ((5, 0.0), (40, 1e-2)):
+        ref, it_ref, _ = CG.shifted_cg(p.A, p.B, theta, X0, lam, max_iter, rtol, rhs=rhs,
+                                       precond=True)
+        rp, ci, val = csr_dev(S)
+        Xd = dev(padded(X0, k + 2))
+        it = g.gcge_block_cg_f64(n, rp, ci, val, k, dev(rhs), k, Xd, k + 2, max_iter, rtol,
+                                 precond=g.GCGE_PRECOND_JACOBI)
+        torch.cuda.synchronize()
+        assert np.array_equal(it, it_ref)
+        got = host(Xd)[:, :k]
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
 def test_block_cg_f32(g):
     import torch
     p = W.make_config("fd3d_128", N=12, seed=2)

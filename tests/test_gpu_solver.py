@@ -191,6 +191,26 @@ def test_solver_alg2_matches_oracle(g, precision):
     assert _check_vectors(X, ev, p.A, p.B) <= 1e-6
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solver_jacobi_precond_matches_oracle(g, precision):
+    """STEP 6 by Jacobi-preconditioned CG, FP64 and mixed, against the oracle run with
+    the same preconditioner, on the lognormal FD pencil."""
+    p = W.make_config("fd3d_128", N=12, seed=5)
+    nev, bs = 16, 4
+    X0 = W.initial_block(p.n, nev + 3 * bs, 3)
+    ev, X, st, status = _solve(g, p, nev, bs, X0, precond=g.GCGE_PRECOND_JACOBI,
+                               precision=precision)
+    ref = G.gcg(p.A, p.B, nev, bs, 1e-8, X0, G.Params(precond=True))
+    assert status == 0 and ref.converged
+    assert np.abs(ev - ref.evals).max() <= 1e-8 * np.abs(ref.evals).max()
+    assert L.residual_norms(p.A, p.B, X, ev).max() < 1e-8
+    assert _check_vectors(X, ev, p.A, p.B) <= 1e-6
+    if precision == 0:
+        # same algorithm: iteration counts close (the lognormal pencil's lambda_max /
+        # lambda_1 ~ 1e5 lets rounding move the trajectories apart, hence 25 %)
+        assert abs(st["iterations"] - ref.iterations) <= max(2, ref.iterations // 4)
+
+
 @pytest.mark.parametrize("kind", ["permuted", "diagonal"])
 def test_union_pattern_differs_from_a(g, kind):
     """S = A - theta B on a union pattern that is not A's own: B = P A P^T (same nnz,
