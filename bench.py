@@ -1,25 +1,37 @@
 #!/usr/bin/env python
-"""Benchmark: time to the nev smallest eigenpairs at relative residual 1e-8.
+"""Benchmark: time to the nev smallest eigenpairs at relative residual 1e-8, mixed
+precision vs FP64 on the GPU, and SpMM GB/s.
 
-Workload: 3D Q1 FEM Laplacian on 64^3 interior nodes (n = 262,144, 27-point
-pattern, nnz = 6,859,000), generalized pencil A = K(x)M(x)M + ..., B = M(x)M(x)M,
-nev = 100, blockSize = 20, seeded synthetic data (no external matrix).
+Headline workload (one step = one complete gcge_solve, Algorithm 1 to convergence):
+the 3D Q1 FEM pencil on 64^3 interior nodes (n = 262,144, 27-point pattern,
+nnz = 6,859,000), A = K(x)M(x)M + ..., B = M(x)M(x)M, nev = 100, blockSize = 20,
+tol 1e-8, seeded synthetic data.  The matrices are resident in HBM; a 256 MB buffer
+(> L2) is written before every timed step.  ``value`` is the median mixed-precision
+time to solution over the timed steps (the solves run without per-kernel events);
+``fp64`` the median of the plain FP64 GPU path; ``e2e`` the same mixed solve through
+the public API from host CSR (create with the CSR upload, solve, eigenvalues and
+eigenvectors back to host memory).  One extra profiled solve (events around every
+launch, not timed) gives the kernel classes and the roofline of the dominant one.
 
-One step = one complete gcge_solve (Algorithm 1 to convergence) with the
-matrices already resident in HBM.  ``value`` is the mixed-precision time to
-solution (seconds, lower is better); the plain FP64 GPU path is reported
-beside it.  ``e2e`` repeats the measurement through the public C API from host
-buffers: gcge_create (CSR upload), gcge_solve and gcge_eigenpairs (eigenvalues
-and eigenvectors back to the host) inside the timed region.
+``largest`` (on by default, --no-largest skips it): one mixed solve of the largest
+single-GPU workload, Q1 on 160^3 nodes with a lognormal coefficient (n = 4,096,000,
+nnz = 109,215,352), nev = 1000, blockSize = 100, moving mechanism, with FP64
+residuals of 16 eigenpairs recomputed on the host.  Its solve takes minutes, so the
+driver's --steps/--warmup repeat the headline workload, not this one.
 
-``--impl reference`` times the FP64 CPU oracle instead (a bounded sample per step,
-scaled to the time-to-solution unit).
+``--impl reference`` times the FP64 CPU oracle (the reference arm; there is no code of
+the paper to run): each step runs its start-up and first two GCG iterations on the
+same workload; the line's value extrapolates the per-iteration time to a whole solve
+(see ``cpu_baseline.sample``), ms_per_step is what a step actually took.
+``--table`` runs every synthetic workload once (mixed and FP64) and prints one JSON
+line per run (the per-config table).
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,6 +45,18 @@ import numpy as np  # noqa: E402
 
 METRIC = "time to nev eigenpairs at rel. residual 1e-8: mixed vs FP64 GPU; SpMM GB/s"
 WORKLOAD = "q1_64"
+LARGEST = "q1_160"
+DESCR = {
+    "fd2d_64": "fd2d_64: 5-point FD 64^2 (n=4096), B=I, nev=20, blockSize=10",
+    "q1_64": "q1_64: Q1 FEM 64^3 (n=262144, nnz=6859000), B=consistent mass, nev=100, "
+             "blockSize=20, tol=1e-8 relative residual",
+    "fd3d_128": "fd3d_128: 7-point FD 128^3 (n=2097152), lognormal coefficient, lumped "
+                "mass +-10%, nev=200, blockSize=40",
+    "q1grad_48": "q1grad_48: Q1 FEM 48^3 (n=110592), coefficient exp(0.5 N(0,1)), nev=10, "
+                 "blockSize=2",
+    "q1_160": "q1_160: Q1 FEM 160^3 (n=4096000, nnz=109215352), lognormal coefficient "
+              "(sigma=1), consistent mass, nev=1000, blockSize=100, moving mechanism",
+}
 
 
 def parse():
@@ -42,13 +66,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=WORKLOAD)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-profile", action="store_true",
-                    help="no per-kernel CUDA-event profile (fewer API calls under ncu)")
+    ap.add_argument("--no-largest", action="store_true")
+    ap.add_argument("--table", action="store_true",
+                    help="one mixed and one FP64 solve of every workload, one JSON line each")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["spmm32", "spmm64", "gram_tc", "vc_tc", "gram64", "vc64"],
+                    choices=["spmm32", "spmm64", "gram_tc", "vc_tc", "gram64", "vc64",
+                             "gram64tc", "vc64tc", "cg32"],
                     help="run one kernel class three times on the workload's shapes (for ncu)")
     return ap.parse_args()
 
@@ -89,6 +115,24 @@ def workload(name):
     return p, nev, bs
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            for key in ("model name", "CPU part"):
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 # ------------------------------------------------------------------ clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -124,34 +168,45 @@ class Clocks:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_lines(open(self.path).read().splitlines())
 
 
-# FP64 arithmetic peak of GB300 (nominal; the FP64 classes are bound by it, not by HBM)
+def parse_clock_lines(lines):
+    """Median SM clock, max clock and the throttle reasons seen in nvidia-smi CSV lines."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ rooflines
+# FP64 arithmetic peak of GB300 derived from its unit count and clock: FP64 FMA runs
+# at 1/64 of the 128 FP32 lanes of an SM, i.e. 2 FMA = 4 flop per clock per SM, and
+# 152 SMs x 2.07 GHz x 4 = 1.26 TFLOP/s (NVIDIA's nominal figure is 1.25).
 FP64_PEAK_TFLOPS = 1.25
+# Digit-plane products per FP64 product in the tensor-core FP64 emulation (pairs of the
+# seven 7-bit digits with i + j <= 8): their bf16 flops are 28 x the FP64 flops.
+OZ_PAIRS = 28
 
-# DRAM traffic (read + write) over algorithmic bytes, per kernel class, from one full
-# ncu capture of each class on the q1_64 shapes (profiles/kernels_q1_64_shapes.md);
-# traffic per launch = this ratio x the class's algorithmic bytes per launch.
-TRAFFIC_RATIO = {"q1_64": {"spmm": 0.84, "gram": 1.05, "vc": 0.88, "spmm64": 0.98,
-                           "gram64": 1.01, "vc64": 3.30}}
+# DRAM traffic (read + write) over algorithmic bytes per kernel class, measured by ncu
+# on each class's kernel at the headline workload's shapes (summaries in profiles/);
+# None where the kernel changed after its counters were taken.
+TRAFFIC_RATIO = {"q1_64": {"spmm": None, "gram": 1.05, "vc": 0.88, "spmm64": None,
+                           "gram64": 1.01, "vc64": 3.30, "gram64tc": None, "vc64tc": None}}
 
 
 def traffic_per_launch(config, cls, prof):
@@ -161,25 +216,29 @@ def traffic_per_launch(config, cls, prof):
     return round(r * prof["bytes"] / prof["calls"])
 
 
-def kernel_rooflines(prof, hbm, src):
+def kernel_rooflines(prof, peaks):
     """Per kernel class: time share and achieved rate against its own roof."""
+    hbm, bf16_sust, src = peaks["hbm"], peaks["bf16_sustained"], peaks["source"]
     out = {}
     for k, v in prof.items():
         if k in ("syev", "other") or v["calls"] == 0 or v["ms"] <= 0:
             continue
-        if k.endswith("64") and k != "spmm64":
-            ach = v["flops"] / (v["ms"] / 1e3) / 1e12
+        sec = v["ms"] / 1e3
+        if k.endswith("tc") and k.startswith(("gram64", "vc64")):
+            ach = OZ_PAIRS * v["flops"] / sec / 1e12
+            out[k] = {"bound": "tensor", "achieved": round(ach, 1), "peak": bf16_sust,
+                      "unit": "TFLOP/s", "frac": round(ach / bf16_sust, 4),
+                      "peak_source": f"{src} bf16 sustained",
+                      "fp64_equiv_tflops": round(v["flops"] / sec / 1e12, 2)}
+        elif k in ("gram64", "vc64") or (
+                k == "spmm64" and v["flops"] / sec / 1e12 / FP64_PEAK_TFLOPS >
+                v["bytes"] / sec / 1e9 / hbm):
+            ach = v["flops"] / sec / 1e12
             out[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": FP64_PEAK_TFLOPS,
                       "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                      "peak_source": "nominal FP64 rate"}
-        elif k == "spmm64" and v["flops"] / (v["ms"] / 1e3) / 1e12 / FP64_PEAK_TFLOPS > \
-                v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm:
-            ach = v["flops"] / (v["ms"] / 1e3) / 1e12
-            out[k] = {"bound": "alu", "achieved": round(ach, 3), "peak": FP64_PEAK_TFLOPS,
-                      "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                      "peak_source": "nominal FP64 rate"}
+                      "peak_source": "FP64 rate from unit count and clock"}
         else:
-            ach = v["bytes"] / (v["ms"] / 1e3) / 1e9
+            ach = v["bytes"] / sec / 1e9
             out[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                       "frac": round(ach / hbm, 4), "peak_source": src}
         out[k].update(ms=round(v["ms"], 2), calls=int(v["calls"]))
@@ -190,124 +249,120 @@ def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
-    return 6800.0, 1900.0, "fallback"
+        return {"hbm": d.get("hbm_gbs", 6800.0), "bf16": d.get("bf16_tflops", 1900.0),
+                "bf16_sustained": d.get("bf16_tflops_sustained", d.get("bf16_tflops", 1700.0)),
+                "source": "measured"}
+    return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
 
 
 # ------------------------------------------------------------------ ours
+def solve_times(g, torch, p, nev, bs, precision, steps, warmup, stream, flush, evd, world,
+                **opts):
+    """Median-ready per-solve device times (CUDA events on the solve's stream)."""
+    s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=precision, seed=0, **opts)
+    for _ in range(warmup):
+        flush.zero_()
+        s.solve(evecs_device=evd)
+    ms, its, launches = [], [], 0
+    for _ in range(steps):
+        flush.zero_()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.solve(evecs_device=evd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms.append(e0.elapsed_time(e1))
+        st = s.stats()
+        its.append(st["iterations"])
+        launches += st["kernel_launches"]
+    st = s.stats()
+    ev, _ = g.gcge_eigenpairs(s.h, nev, p.n, evd, True)
+    s.close()
+    return ms, its, launches, st, ev
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2111_06552_gb300 as g
+    import workloads as W
 
     torch.cuda.set_device(local)
     g.lib()
     p, nev, bs = workload(args.config)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-
-    def make(precision):
-        return g.Solver(p.A, p.B, nev, bs, 1e-8, precision=precision, seed=0,
-                        profile=0 if args.no_profile else 1)
-
-    def timed(solver, steps, warmup):
-        for _ in range(warmup):
-            flush.zero_()
-            solver.solve(evecs_device=evd)
-        ms = []
-        prof_tot = None
-        its = []
-        for _ in range(steps):
-            flush.zero_()
-            barrier(world)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solver.solve(evecs_device=evd)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            barrier(world)
-            ms.append(e0.elapsed_time(e1))
-            st = solver.stats()
-            its.append(st["iterations"])
-            if prof_tot is None:
-                prof_tot = {k: dict(v) for k, v in st["prof"].items()}
-                launches = st["kernel_launches"]
-                stats0 = st
-            else:
-                for k, v in st["prof"].items():
-                    for f in v:
-                        prof_tot[k][f] += v[f]
-                launches += st["kernel_launches"]
-        return ms, prof_tot, launches, its, stats0
-
     evd = torch.empty((nev, p.n), dtype=torch.float64, device="cuda")
-    res = {}
     with Clocks(local) as clk:
-        sm = make(g.GCGE_MIXED)
-        ms_mx, prof_mx, launches_mx, its_mx, st_mx = timed(sm, args.steps, args.warmup)
-        ev_mx, _ = g.gcge_eigenpairs(sm.h, nev, p.n, evd, True)
-        sm.close()
-        ms_64, its_64 = [float("nan")], [None]
+        ms_mx, its_mx, launches_mx, st_mx, ev_mx = solve_times(
+            g, torch, p, nev, bs, g.GCGE_MIXED, args.steps, args.warmup, stream, flush, evd,
+            world)
+        ms_64, its_64, ev_64 = [float("nan")], [None], None
         if args.fp64_steps > 0:
-            s64 = make(g.GCGE_FP64)
-            ms_64, prof_64, launches_64, its_64, st_64 = timed(s64, args.fp64_steps, 1)
-            s64.close()
+            ms_64, its_64, _, _, ev_64 = solve_times(
+                g, torch, p, nev, bs, g.GCGE_FP64, args.fp64_steps, 1, stream, flush, evd, world)
     clocks = clk.summary()
-    # accuracy of the timed result against the closed-form spectrum
-    import workloads as W
+    # profiled solve (events around every launch; not timed): kernel classes, roofline
+    sp = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=g.GCGE_MIXED, seed=0, profile=1)
+    sp.solve(evecs_device=evd)
+    prof = sp.stats()["prof"]
+    sp.close()
+
     exact = W.q1_eigs(64, nev) if args.config == "q1_64" else None
     err = float(np.abs(ev_mx - exact).max() / exact[0]) if exact is not None else None
+    err64 = (float(np.abs(ev_mx - ev_64).max() / np.abs(ev_64).max())
+             if ev_64 is not None else None)
 
-    t_mx = max_over_ranks(float(np.mean(ms_mx)) / 1e3, world)
-    t_64 = max_over_ranks(float(np.mean(ms_64)) / 1e3, world)
-
-    # roofline of the dominant kernel class inside the timed mixed solves
-    hbm, bf16, src = measured_peaks()
-    kernels = kernel_rooflines(prof_mx, hbm, src)
-    if not kernels:   # --no-profile: no per-kernel times
-        kernels = {"none": {"bound": None, "achieved": None, "peak": None, "unit": None,
-                            "frac": None, "peak_source": None, "ms": 0.0, "calls": 0}}
+    t_mx = max_over_ranks(float(np.median(ms_mx)) / 1e3, world)
+    t_64 = max_over_ranks(float(np.median(ms_64)) / 1e3, world)
+    peaks = measured_peaks()
+    kernels = kernel_rooflines(prof, peaks)
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
-    spmm = prof_mx["spmm"]
+    spmm = prof["spmm"]
     spmm_gbs = spmm["bytes"] / (spmm["ms"] / 1e3) / 1e9 if spmm["ms"] > 0 else 0.0
-    tot_ms = sum(v["ms"] for v in prof_mx.values())
+    tot_ms = sum(v["ms"] for v in prof.values())
     roof = {"bound": d["bound"], "kernel": dom, "achieved": d["achieved"], "peak": d["peak"],
             "unit": d["unit"], "frac": d["frac"], "peak_source": d["peak_source"],
-            "traffic": traffic_per_launch(args.config, dom, prof_mx.get(dom)),
-            "avg_launch_us": round(1e3 * d["ms"] / max(d["calls"], 1), 2)}
-    res.update(t_mx=t_mx, t_64=t_64)
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(g, p, nev, bs, args, stream)
+            "traffic": traffic_per_launch(args.config, dom, prof.get(dom)),
+            "avg_launch_us": round(1e3 * d["ms"] / max(d["calls"], 1), 2),
+            "timed_in": "one profiled mixed solve (CUDA events on the solve's stream)"}
+    e2e = None if args.no_e2e else run_e2e(g, p, nev, bs, args)
     line = {
         "metric": METRIC, "value": round(t_mx, 5), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_mx, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "q1_64: Q1 FEM 64^3 (n=262144, nnz=6859000), B=consistent mass, "
-                               "nev=100, blockSize=20, tol=1e-8 relative residual",
-                   "precision": "mixed (FP32 SpMM/CG/Gram/update, FP64 small dense + FP64 refinement)",
+        "config": {"workload": DESCR[args.config],
+                   "precision": "mixed (FP32 SpMM/CG/Gram/update, FP64 small dense + FP64 "
+                                "phase with tensor-core FP64 products)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "256 MB buffer written between timed steps"},
+                   "l2": "256 MB buffer written before every timed step",
+                   "statistic": "median of the timed solves"},
         "fp64": {"value": round(t_64, 5), "unit": "s", "dtype": "f64",
-                 "iterations": its_64[0], "steps": args.fp64_steps},
+                 "iterations": its_64[0], "steps": args.fp64_steps, "statistic": "median"},
         "iterations": its_mx[0], "iterations_fp32": st_mx["iterations_fp32"],
         "max_rel_eig_err_vs_closed_form": err,
+        "max_rel_eig_diff_mixed_vs_fp64": err64,
         "spmm_gbs": round(spmm_gbs, 1),
         "roofline": roof,
-        "kernel_share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof_mx.items()} if tot_ms else {},
+        "kernel_share": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()} if tot_ms else {},
         "kernels": kernels,
         "gpu_launches": int(launches_mx),
         "clocks": clocks,
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_largest and world == 1:
+        del evd
+        torch.cuda.empty_cache()
+        line["largest"] = run_largest(g, torch, stream)
     return line
 
 
-def run_e2e(g, p, nev, bs, args, stream):
+def run_e2e(g, p, nev, bs, args):
     """Public-API solve from host buffers: create (H2D CSR), solve, eigenpairs (D2H)."""
     import torch
     csr_bytes = 0
@@ -324,21 +379,65 @@ def run_e2e(g, p, nev, bs, args, stream):
         torch.cuda.synchronize()
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    return {"value": round(float(np.mean(times)), 5), "unit": "s", "h2d_bytes_per_step": int(csr_bytes),
-            "d2h_bytes_per_step": int(out_bytes)}
+    return {"value": round(float(np.median(times)), 5), "unit": "s",
+            "h2d_bytes_per_step": int(csr_bytes), "d2h_bytes_per_step": int(out_bytes),
+            "statistic": "median"}
+
+
+def run_largest(g, torch, stream):
+    """One mixed solve of the largest workload, with host-side FP64 residuals."""
+    import workloads as W
+    p, nev, bs = workload(LARGEST)
+    evd = torch.empty((nev, p.n), dtype=torch.float64, device="cuda")
+    s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=g.GCGE_MIXED, seed=0, profile=1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    status = g.gcge_solve(s.h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ev, nconv = g.gcge_eigenpairs(s.h, nev, p.n, evd, True)
+    st = s.stats()
+    s.close()
+    cols = sorted(set(np.linspace(0, nev - 1, 16).astype(int).tolist()))
+    X = evd[cols].cpu().numpy().T
+    AX, BX = p.A @ X, p.B @ X
+    lam = ev[cols]
+    res = np.linalg.norm(AX - BX * lam, axis=0) / (np.abs(lam) * np.sqrt(np.einsum("ij,ij->j", X, BX)))
+    spmm = st["prof"]["spmm"]
+    del evd
+    torch.cuda.empty_cache()
+    return {"workload": DESCR[LARGEST], "status": int(status), "nconv": int(nconv),
+            "value": round(e0.elapsed_time(e1) / 1e3, 2), "unit": "s", "solves": 1,
+            "iterations": st["iterations"], "iterations_fp32": st["iterations_fp32"],
+            "cg_steps": st["cg_steps"], "moves": st["moves"],
+            "max_sampled_rel_residual": float(res.max()), "sampled_columns": len(cols),
+            "spmm_gbs": round(spmm["bytes"] / (spmm["ms"] / 1e3) / 1e9, 1) if spmm["ms"] else None,
+            "class_ms": {k: round(v["ms"], 1) for k, v in st["prof"].items() if v["ms"] > 0},
+            "note": "one solve per bench run (minutes); timed with per-kernel events on"}
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_sample(config, iters=2):
-    """Time the FP64 oracle on the first `iters` GCG iterations of the workload."""
+def oracle_sample(config):
+    """The FP64 oracle's start-up and first two GCG iterations on the workload.
+
+    Returns (wall seconds of the sample, start-up seconds, seconds of one whole GCG
+    iteration) -- the iteration is the first one, timed from its STEP 3 to the STEP 3
+    of the second, which the sample reaches before it stops."""
     import workloads as W
     from oracle.gcg import gcg, Params
     p, nev, bs = workload(config)
     X0 = W.initial_block(p.n, nev + 3 * bs, 0)
+    marks = {}
+
+    def trace(e):
+        if e["step"] == 3:
+            marks[e["it"]] = time.perf_counter()
+
     t0 = time.perf_counter()
-    r = gcg(p.A, p.B, nev, bs, 1e-8, X0, Params(max_iter=iters))
-    dt = time.perf_counter() - t0
-    return dt, r.iterations
+    gcg(p.A, p.B, nev, bs, 1e-8, X0, Params(max_iter=2, trace=trace))
+    t1 = time.perf_counter()
+    return t1 - t0, marks[1] - t0, marks[2] - marks[1]
 
 
 def oracle_iterations(config):
@@ -348,40 +447,91 @@ def oracle_iterations(config):
     return None
 
 
+def oracle_threads():
+    """Threads the oracle's dense algebra may use (BLAS); its sparse products are
+    single-threaded (scipy.sparse)."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
+
+
 def cpu_baseline(config, gpu_iters):
-    dt, it = oracle_sample(config)
+    wall, init, per_it = oracle_sample(config)
     iters = oracle_iterations(config) or gpu_iters
-    per_it = dt / it
-    return {"value": round(per_it * iters, 2), "unit": "s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"first {it} GCG iterations of the same workload (incl. the initial "
-                      f"orthonormalisation) took {dt:.1f} s; scaled by {iters} iterations to solution"}
+    value = init + per_it * iters
+    return {"value": round(value, 2), "unit": "s", "cores": oracle_threads(),
+            "sparse_threads": 1, "cpu_model": cpu_model(), "kind": "oracle",
+            "sample": f"start-up ({init:.1f} s) and first GCG iteration ({per_it:.1f} s) of the "
+                      f"FP64 oracle on the same workload; value = start-up + {iters} "
+                      f"iterations (the iteration count of a full oracle run of this "
+                      f"workload); the sample took {wall:.1f} s"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    times = []
+    walls, inits, its = [], [], []
     for i in range(args.warmup + args.steps):
-        dt, it = oracle_sample(args.config, iters=1 if i < args.warmup else 2)
+        wall, init, per_it = oracle_sample(args.config)
         if i >= args.warmup:
-            times.append(dt / it)
+            walls.append(wall)
+            inits.append(init)
+            its.append(per_it)
     iters = oracle_iterations(args.config) or 60
-    v = float(np.mean(times)) * iters
+    v = float(np.median(inits)) + float(np.median(its)) * iters
+    ms_step = 1e3 * float(np.median(walls))
+    cb = {"value": round(v, 2), "unit": "s", "cores": oracle_threads(), "sparse_threads": 1,
+          "cpu_model": cpu_model(), "kind": "oracle",
+          "sample": f"each step: the FP64 oracle's start-up and first two GCG iterations on "
+                    f"the same workload ({ms_step / 1e3:.1f} s, the step's own time); value = "
+                    f"start-up + {iters} whole iterations (median per-iteration time; "
+                    f"{iters} = iterations of a full oracle run)"}
     return {"metric": METRIC, "value": round(v, 2), "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * v, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "q1_64: Q1 FEM 64^3 (n=262144, nnz=6859000), nev=100, "
-                                   "blockSize=20, tol=1e-8"},
-            "cpu_baseline": {"value": round(v, 2), "unit": "s", "cores": os.cpu_count(),
-                             "kind": "oracle",
-                             "sample": f"per step: 2 GCG iterations of the FP64 oracle, "
-                                       f"scaled by {iters} iterations to solution"},
+            "config": {"workload": DESCR[args.config], "statistic": "median"},
+            "cpu_baseline": cb,
             "e2e": {"value": round(v, 2), "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ per-config table
+def run_table():
+    """One mixed and one FP64 solve (after one warm-up each) of every workload."""
+    import torch
+    import paper_2111_06552_gb300 as g
+    g.lib()
+    stream = torch.cuda.current_stream()
+    for name in ("fd2d_64", "q1_64", "fd3d_128", "q1grad_48", "q1_160"):
+        p, nev, bs = workload(name)
+        for prec, tag in ((g.GCGE_MIXED, "mixed"), (g.GCGE_FP64, "fp64")):
+            s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0, profile=1)
+            if name != "q1_160":
+                s.solve()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            status = g.gcge_solve(s.h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = s.stats()
+            ev, nconv = g.gcge_eigenpairs(s.h, nev, p.n)
+            s.close()
+            prof = st["prof"]
+            peaks = measured_peaks()
+            ks = kernel_rooflines(prof, peaks)
+            print(json.dumps({"workload": name, "precision": tag, "status": int(status),
+                              "seconds": round(e0.elapsed_time(e1) / 1e3, 3),
+                              "iterations": st["iterations"], "nconv": int(nconv),
+                              "evals_head": [float(x) for x in ev[:3]],
+                              "evals": [float(x) for x in ev],
+                              "kernels": ks}), flush=True)
+
+
+# ------------------------------------------------------------------ ncu cases
 def kernel_case(args):
     """Three launches of one kernel class on the benchmark workload's shapes, no timing:
     the command that the committed ncu summaries capture."""
@@ -402,13 +552,20 @@ def kernel_case(args):
             Y = torch.empty(n, k, device="cuda", dtype=dt)
             f = g.gcge_spmm_f32 if dt == torch.float32 else g.gcge_spmm_f64
             f(n, rp, ci, val, k, 1.0, X, k, 0.0, Y, k)
-        elif args.kernel_case in ("gram_tc", "gram64"):
+        elif args.kernel_case == "cg32":
+            val = torch.tensor(p.A.data, device="cuda").float()
+            Bm = torch.randn(n, k, device="cuda")
+            X = torch.zeros(n, k, device="cuda")
+            g.gcge_block_cg_f32(n, rp, ci, val, k, Bm, k, X, k, 2, 1e-30)
+        elif args.kernel_case in ("gram_tc", "gram64", "gram64tc"):
             dt = torch.float32 if args.kernel_case == "gram_tc" else torch.float64
             X = torch.randn(n, d, device="cuda", dtype=dt)
             Y = torch.randn(n, k, device="cuda", dtype=dt)
             C = torch.zeros(k, d, device="cuda", dtype=torch.float64)
-            if dt == torch.float32:
+            if args.kernel_case == "gram_tc":
                 g.gcge_gram_f32(n, d, k, 1.0, X, d, Y, k, 0.0, C, d, tc=1)
+            elif args.kernel_case == "gram64tc":
+                g.gcge_gram_f64_tc(n, d, k, 1.0, X, d, Y, k, 0.0, C, d)
             else:
                 g.gcge_gram_f64(n, d, k, 1.0, X, d, Y, k, 0.0, C, d)
         else:
@@ -416,8 +573,10 @@ def kernel_case(args):
             V = torch.randn(n, d, device="cuda", dtype=dt)
             Cm = torch.randn(q, d, device="cuda", dtype=torch.float64)
             Z = torch.empty(n, q, device="cuda", dtype=dt)
-            if dt == torch.float32:
+            if args.kernel_case == "vc_tc":
                 g.gcge_vc_f32(n, d, q, 1.0, V, d, Cm, d, 0.0, Z, q, tc=1)
+            elif args.kernel_case == "vc64tc":
+                g.gcge_vc_f64_tc(n, d, q, 1.0, V, d, Cm, d, 0.0, Z, q)
             else:
                 g.gcge_vc_f64(n, d, q, 1.0, V, d, Cm, d, 0.0, Z, q)
     torch.cuda.synchronize()
@@ -428,6 +587,9 @@ def main():
     args = parse()
     if args.kernel_case:
         kernel_case(args)
+        return
+    if args.table:
+        run_table()
         return
     rank, world, local = dist_init(args.gpus)
     if args.impl == "reference":

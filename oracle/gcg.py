@@ -59,8 +59,9 @@ class Params:
     orth: OrthParams = field(default_factory=OrthParams)
     orth_alg: int = 3            # STEP 2 by Algorithm 3 (default) or Algorithm 2
     precond: bool = False        # STEP 6 by Jacobi-preconditioned CG (oracle/cg.py)
-    # optional observer called with a dict at STEP 5 and STEP 6 (tests read the
-    # iteration's intermediate blocks through it; it never changes the iteration)
+    # optional observer called with a dict at the start of STEP 3 and at STEPs 5 and 6
+    # (tests read the iteration's blocks through it, the benchmark its timing; it never
+    # changes the iteration)
     trace: object = None
 
 
@@ -128,6 +129,8 @@ def gcg(A, B, nev: int, bs: int, tol: float, X0: np.ndarray, params: Params = Pa
     converged = False
     while True:
         it += 1
+        if p.trace is not None:
+            p.trace(dict(step=3, it=it))
         # ---- STEP 3: Rayleigh-Ritz on V_a = [X_a, P, W] with an explicit V^T A V
         Va = np.hstack([X[:, lw:], P, W])
         AVa = spmm(A, Va)

@@ -539,6 +539,8 @@ def _step5_pin(pencil, nev, bs, seed, max_iter, moving=False):
         if e["step"] == 6:
             xn_prev = e["Xn"]
             continue
+        if e["step"] != 5:
+            continue
         Xnew, c, b, P = e["Xnew"], e["c"], e["bs_new"], e["P"]
         Vxn = Xnew[:, c:c + b]
         Pt = Vxn - xn_prev @ (xn_prev.T @ Bm(Vxn))
