@@ -56,6 +56,8 @@ DESCR = {
                  "blockSize=2",
     "q1_160": "q1_160: Q1 FEM 160^3 (n=4096000, nnz=109215352), lognormal coefficient "
               "(sigma=1), consistent mass, nev=1000, blockSize=100, moving mechanism",
+    "rand_200k": "rand_200k: random symmetric pattern (n=200000, ~61 nonzeros per row), "
+                 "diagonally dominant, B=I, nev=50, blockSize=10",
 }
 
 
@@ -505,7 +507,7 @@ def run_table():
     import paper_2111_06552_gb300 as g
     g.lib()
     stream = torch.cuda.current_stream()
-    for name in ("fd2d_64", "q1_64", "fd3d_128", "q1grad_48", "q1_160"):
+    for name in ("fd2d_64", "q1_64", "fd3d_128", "q1grad_48", "rand_200k", "q1_160"):
         p, nev, bs = workload(name)
         for prec, tag in ((g.GCGE_MIXED, "mixed"), (g.GCGE_FP64, "fp64")):
             s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0, profile=1)

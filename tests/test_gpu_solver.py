@@ -211,6 +211,54 @@ def test_solver_jacobi_precond_matches_oracle(g, precision):
         assert abs(st["iterations"] - ref.iterations) <= max(2, ref.iterations // 4)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_random_pattern_stand_in_matches_oracle(g, precision):
+    """The random-pattern (SuiteSparse-class) stand-in at n = 3000 against the oracle."""
+    p = W.make_config("rand_200k", N=3000, seed=0)
+    nev, bs = 10, 3
+    X0 = W.initial_block(p.n, nev + 3 * bs, 1)
+    ev, X, st, status = _solve(g, p, nev, bs, X0, precision=precision)
+    ref = G.gcg(p.A, None, nev, bs, 1e-8, X0)
+    assert status == 0 and ref.converged
+    assert np.abs(ev - ref.evals).max() <= 1e-8 * np.abs(ref.evals).max()
+    assert L.residual_norms(p.A, None, X, ev).max() < 1e-8
+    assert _check_vectors(X, ev, p.A, None) <= 1e-6
+
+
+def test_fd3d_128_full_size_mixed_vs_fp64(g):
+    """The 128^3 lognormal FD workload (n = 2,097,152, lambda_max / lambda_1 ~ 1e6),
+    nev = 200, blockSize = 40: the mixed and FP64 GPU paths both converge, every mixed
+    eigenvalue is within 1e-8 (relative) of the FP64 one, FP64 residuals of sampled
+    pairs recomputed on the host are below 1e-8; with c = 1 and B = I the same
+    discretisation matches its closed form (reduced nev)."""
+    import torch
+    p = W.make_config("fd3d_128")
+    nev, bs = 200, 40
+    res = {}
+    for prec in (g.GCGE_FP64, g.GCGE_MIXED):
+        evd = torch.empty((nev, p.n), dtype=torch.float64, device="cuda")
+        s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0)
+        ev, _ = s.solve(evecs_device=evd)
+        status = s.status
+        s.close()
+        assert status == 0
+        cols = [0, 1, 50, 99, 150, 198, 199]
+        Xs = evd[cols].cpu().numpy().T
+        r = L.residual_norms(p.A, p.B, Xs, ev[cols])
+        assert r.max() < 1e-8
+        res[prec] = ev
+        del evd
+        torch.cuda.empty_cache()
+    e64, emx = res[g.GCGE_FP64], res[g.GCGE_MIXED]
+    assert np.all(np.abs(emx - e64) <= 1e-8 * np.abs(e64))
+    pc = W.fd3d_var(128)
+    s = g.Solver(pc.A, None, 40, 8, 1e-8, precision=g.GCGE_MIXED, seed=1)
+    ev, _ = s.solve()
+    s.close()
+    exact = W.fd3d_eigs_const(128, 40)
+    assert np.abs(ev - exact).max() <= 1e-8 * exact[0]
+
+
 @pytest.mark.parametrize("kind", ["permuted", "diagonal"])
 def test_union_pattern_differs_from_a(g, kind):
     """S = A - theta B on a union pattern that is not A's own: B = P A P^T (same nnz,

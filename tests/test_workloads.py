@@ -101,3 +101,17 @@ def test_splitmix64_reference_values():
     assert int(W.splitmix64(z)[0]) == 0xE220A8397B1DCDAF
     z = np.array([0x9E3779B97F4A7C15], dtype=np.uint64)
     assert int(W.splitmix64(z)[0]) == 0x6E789E6AA1B965F4
+
+
+def test_random_pattern_stand_in():
+    """The SuiteSparse-class stand-in: symmetric, ~61 nonzeros per row, SPD by
+    diagonal dominance, deterministic in its seed."""
+    p = W.make_config("rand_200k", N=4000, seed=2)
+    A = p.A
+    assert p.B is None and A.shape == (4000, 4000)
+    assert abs(A.nnz / A.shape[0] - 61) < 3
+    assert abs(A - A.T).max() == 0.0
+    off = abs(A).sum(axis=1).A.ravel() - abs(A.diagonal())
+    assert np.all(A.diagonal() > off)              # strictly diagonally dominant
+    q = W.make_config("rand_200k", N=4000, seed=2)
+    assert np.array_equal(q.A.data, A.data) and np.array_equal(q.A.indices, A.indices)

@@ -389,6 +389,9 @@ CONFIGS = {
     "fd3d_128": dict(nev=200, bs=40),
     "q1grad_48": dict(nev=10, bs=2),
     "q1_160": dict(nev=1000, bs=100),
+    # stand-in for the paper's SuiteSparse (PARSEC) class: random symmetric pattern,
+    # about 60 nonzeros per row, diagonally dominant, B = I
+    "rand_200k": dict(nev=50, bs=10),
 }
 
 
@@ -425,6 +428,10 @@ def make_config(name: str, seed: int = 0, N: int | None = None) -> Pencil:
         c = lognormal_cells((NN + 1,) * 3, 0.5, seed)
         p = q1_var(NN, c)
         p.meta["c"] = c
+    elif name.startswith("rand"):
+        NN = N or 200000
+        A = random_sparse_spd(NN, 30.0 / NN, seed)   # ~30 + 30 mirrored + diagonal per row
+        p = Pencil(A, None, name, {"N": NN})
     elif name.startswith("q1_160") or name.startswith("q1var"):
         NN = N or 160
         c = lognormal_cells((NN + 1,) * 3, 1.0, seed)
