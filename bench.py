@@ -24,7 +24,8 @@ the paper to run): each step runs its start-up and first two GCG iterations on t
 same workload; the line's value extrapolates the per-iteration time to a whole solve
 (see ``cpu_baseline.sample``), ms_per_step is what a step actually took.
 ``--table`` runs every synthetic workload once (mixed and FP64) and prints one JSON
-line per run (the per-config table).
+line per run (the per-config table); ``--ablation`` the option studies (dynamic shift,
+CG steps, Algorithm 2 vs 3, preconditioner).
 """
 from __future__ import annotations
 
@@ -74,6 +75,8 @@ def parse():
     ap.add_argument("--no-largest", action="store_true")
     ap.add_argument("--table", action="store_true",
                     help="one mixed and one FP64 solve of every workload, one JSON line each")
+    ap.add_argument("--ablation", action="store_true",
+                    help="shift / CG-step / orthogonaliser / preconditioner studies")
     ap.add_argument("--kernel-case", default=None,
                     choices=["spmm32", "spmm64", "gram_tc", "vc_tc", "gram64", "vc64",
                              "gram64tc", "vc64tc", "cg32"],
@@ -533,6 +536,58 @@ def run_table():
                               "kernels": ks}), flush=True)
 
 
+# ------------------------------------------------------------------ ablations
+def run_ablation():
+    """The paper's option studies on the synthetic workloads, one solve each (after one
+    warm-up solve of the workload): dynamic shift on/off x CG steps per GCG iteration
+    (Section 4.1, Table 3), Algorithm 2 vs Algorithm 3 (Table 8), and the Jacobi-
+    preconditioned inner solve.  One JSON line per solve with the per-STEP split."""
+    import torch
+    import paper_2111_06552_gb300 as g
+    g.lib()
+    stream = torch.cuda.current_stream()
+    runs = []
+    for name, cgs in (("fd2d_64", (5, 10, 20, 30)), ("q1_64", (5, 10, 20, 30)),
+                      ("fd3d_128", (10, 30))):
+        for shift in (1, 0):
+            for cg in cgs:
+                runs.append((name, g.GCGE_MIXED, dict(use_shift=shift, cg_max_iter=cg)))
+        for prec in (g.GCGE_FP64, g.GCGE_MIXED):
+            runs.append((name, prec, dict(orth=g.GCGE_ORTH_ALG2)))
+            runs.append((name, prec, dict(orth=g.GCGE_ORTH_ALG3)))
+        runs.append((name, g.GCGE_MIXED, dict(precond=g.GCGE_PRECOND_JACOBI)))
+    warmed = set()
+    cache = {}
+    for name, prec, opts in runs:
+        if name not in cache:
+            cache.clear()
+            cache[name] = workload(name)
+        p, nev, bs = cache[name]
+        if name not in warmed:
+            s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0)
+            s.solve()
+            s.close()
+            warmed.add(name)
+        s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0, **opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status = g.gcge_solve(s.h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        ev, nconv = g.gcge_eigenpairs(s.h, nev, p.n)
+        s.close()
+        print(json.dumps({"workload": name, "precision": "mixed" if prec else "fp64",
+                          **opts, "status": int(status),
+                          "seconds": round(e0.elapsed_time(e1) / 1e3, 3),
+                          "iterations": st["iterations"],
+                          "iterations_fp32": st["iterations_fp32"],
+                          "cg_steps": st["cg_steps"], "nconv": int(nconv),
+                          "ms_step": [round(x, 1) for x in st["ms_step"]],
+                          "ev_sum": float(np.sum(ev))}), flush=True)
+
+
 # ------------------------------------------------------------------ ncu cases
 def kernel_case(args):
     """Three launches of one kernel class on the benchmark workload's shapes, no timing:
@@ -592,6 +647,9 @@ def main():
         return
     if args.table:
         run_table()
+        return
+    if args.ablation:
+        run_ablation()
         return
     rank, world, local = dist_init(args.gpus)
     if args.impl == "reference":
