@@ -308,7 +308,9 @@ __global__ void jacobi_inverse_kernel(int64_t n, const int32_t *__restrict__ rp,
 int upd_grid(int64_t n, int k) {
   const int rpp = kCgThreads / (k < kCgThreads ? k : kCgThreads);
   int64_t g = (n + (int64_t)rpp * 4 - 1) / ((int64_t)rpp * 4);
-  const int64_t cap = (int64_t)device_sm_count() * 8;
+  // two CTAs per SM: enough to stream the vectors, and few partial rows for the
+  // last CTA to sum
+  const int64_t cap = (int64_t)device_sm_count() * 2;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

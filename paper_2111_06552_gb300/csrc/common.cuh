@@ -99,8 +99,17 @@ __device__ __forceinline__ bool last_cta_reduce(int k, const double *part, unsig
     const int slots = blockDim.x / kc;
     const int slot = threadIdx.x / kc, j = j0 + threadIdx.x % kc;
     double s = 0.0;
-    if (slot < slots)
-      for (int b = slot; b < nb; b += slots) s += __ldcg(part + (int64_t)b * k + j);
+    if (slot < slots) {
+      // four independent sums in flight (fixed order), then combined
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      int b = slot;
+      for (; b + 3 * slots < nb; b += 4 * slots) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[u] += __ldcg(part + (int64_t)(b + u * slots) * k + j);
+      }
+      for (; b < nb; b += slots) s4[0] += __ldcg(part + (int64_t)b * k + j);
+      s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    }
     sh[threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.x < kc) {

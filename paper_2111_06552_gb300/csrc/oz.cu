@@ -95,47 +95,56 @@ oz_slice_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, i
     }
   }
   __syncthreads();
-  const int i = t / kSlSeg, seg = t % kSlSeg;
+  // a warp takes 32 consecutive rows of one 32-entry segment: conflict-free reads of
+  // the tile (odd row stride) and the segment maxima combined through shared memory
+  const int i = t % kSlRows, seg = t / kSlRows;
   const unsigned long long *row = tile + i * LD + seg * 32;
   unsigned long long mx = 0;
 #pragma unroll 8
   for (int kk = 0; kk < 32; ++kk) mx = max(mx, row[kk] & 0x7FFFFFFFFFFFFFFFull);
+  __shared__ unsigned long long smax[kSlSeg][kSlRows];
+  smax[seg][i] = mx;
+  __syncthreads();
 #pragma unroll
-  for (int o = 1; o < kSlSeg; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+  for (int q = 0; q < kSlSeg; ++q) mx = max(mx, smax[q][i]);
   const int exmax = (int)(mx >> 52);
   const int Ex = mx == 0 ? kExpZero : exmax - 1022;     // max < 2^Ex
   if (seg == 0) E[blockIdx.x * (int64_t)Rp + i0 + i] = Ex;
-  unsigned long long F[32];   // |x| / 2^Ex in 49 fraction bits, per entry of the segment
-  uint32_t signs = 0;
 #pragma unroll
-  for (int kk = 0; kk < 32; ++kk) {
-    const unsigned long long u = row[kk];
-    const int ex = (int)((u >> 52) & 0x7FF);
-    signs |= (uint32_t)(u >> 63) << kk;
-    unsigned long long f = 0;
-    if (ex != 0 && Ex != kExpZero) {
-      const int sh = 1026 + Ex - ex;                      // >= 4 since |x| < 2^Ex
-      const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-      // rounded to nearest (no bias toward zero); the top value stays below 2^49
-      f = sh < 64 ? ((mant + (1ull << (sh - 1))) >> sh) : 0ull;
-      f = f > 0x1FFFFFFFFFFFFull ? 0x1FFFFFFFFFFFFull : f;
-    }
-    F[kk] = f;
-  }
+  for (int half = 0; half < 2; ++half) {
+    unsigned long long F[16];   // |x| / 2^Ex in 49 fraction bits, 16 entries at a time
+    uint32_t signs = 0;
 #pragma unroll
-  for (int p = 0; p < kDigits; ++p) {
-    uint4 *dst = reinterpret_cast<uint4 *>(P + ((int64_t)p * Rp + i0 + i) * Kp + k0 + seg * 32);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t w[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int k1 = 8 * q + 2 * h, k2 = k1 + 1;
-        const uint32_t a = digit_bf16((uint32_t)(F[k1] >> (42 - 7 * p)) & 127u, p, (signs >> k1) & 1u);
-        const uint32_t b = digit_bf16((uint32_t)(F[k2] >> (42 - 7 * p)) & 127u, p, (signs >> k2) & 1u);
-        w[h] = a | (b << 16);
+    for (int kk = 0; kk < 16; ++kk) {
+      const unsigned long long u = row[16 * half + kk];
+      const int ex = (int)((u >> 52) & 0x7FF);
+      signs |= (uint32_t)(u >> 63) << kk;
+      unsigned long long f = 0;
+      if (ex != 0 && Ex != kExpZero) {
+        const int sh = 1026 + Ex - ex;                      // >= 4 since |x| < 2^Ex
+        const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        // rounded to nearest (no bias toward zero); the top value stays below 2^49
+        f = sh < 64 ? ((mant + (1ull << (sh - 1))) >> sh) : 0ull;
+        f = f > 0x1FFFFFFFFFFFFull ? 0x1FFFFFFFFFFFFull : f;
       }
-      dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+      F[kk] = f;
+    }
+#pragma unroll
+    for (int p = 0; p < kDigits; ++p) {
+      uint4 *dst = reinterpret_cast<uint4 *>(P + ((int64_t)p * Rp + i0 + i) * Kp + k0 + seg * 32 +
+                                             16 * half);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int k1 = 8 * q + 2 * h, k2 = k1 + 1;
+          const uint32_t a = digit_bf16((uint32_t)(F[k1] >> (42 - 7 * p)) & 127u, p, (signs >> k1) & 1u);
+          const uint32_t b = digit_bf16((uint32_t)(F[k2] >> (42 - 7 * p)) & 127u, p, (signs >> k2) & 1u);
+          w[h] = a | (b << 16);
+        }
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
     }
   }
 }
@@ -289,23 +298,31 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
       for (int jb = 0; jb < kMaxN; jb += 8) {
         if (jb < N) {
-          long long T[8], Lw[8];
-          float gv[8];
+          // the seven accumulators' 8 columns in one batch of loads, one wait
+          uint32_t gv[kGroups][8];
 #pragma unroll
           for (int sd = 0; sd < kGroups; ++sd) {
-            tmem_ld8(tmem + lane_addr + sd * N + jb, gv);
-            const float up = __int_as_float((127 + 7 * sd) << 23);   // 2^(7 sd)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const long long I = (long long)__float2int_rn(gv[u] * up);
-              if (sd == 0) T[u] = I << 28;
-              else if (sd <= 4) T[u] += I << (28 - 7 * sd);
-              else if (sd == 5) Lw[u] = I << 7;
-              else T[u] += (Lw[u] + I + (1ll << 13)) >> 14;   // rounded, not floored
-            }
+            const uint32_t ta = tmem + lane_addr + sd * N + jb;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(gv[sd][0]), "=r"(gv[sd][1]), "=r"(gv[sd][2]), "=r"(gv[sd][3]),
+                  "=r"(gv[sd][4]), "=r"(gv[sd][5]), "=r"(gv[sd][6]), "=r"(gv[sd][7])
+                : "r"(ta));
           }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc[jb + u] += (double)T[u] * pow2(ea + eb[jb + u] - 42);
+          for (int u = 0; u < 8; ++u) {
+            long long T = 0, Lw = 0;
+#pragma unroll
+            for (int sd = 0; sd < kGroups; ++sd) {
+              const float up = __int_as_float((127 + 7 * sd) << 23);   // 2^(7 sd)
+              const long long I = (long long)__float2int_rn(__uint_as_float(gv[sd][u]) * up);
+              if (sd <= 4) T += I << (28 - 7 * sd);
+              else if (sd == 5) Lw = I << 7;
+              else T += (Lw + I + (1ll << 13)) >> 14;   // rounded, not floored
+            }
+            acc[jb + u] += (double)T * pow2(ea + eb[jb + u] - 42);
+          }
         }
       }
       tc_fence_before();

@@ -450,9 +450,10 @@ class Engine {
     return c == GCGE_K_SPMM ? GCGE_K_SPMM64 : c == GCGE_K_GRAM ? GCGE_K_GRAM64 : GCGE_K_VC64;
   }
   // FP64 products of at least this size run on the bf16 tensor cores from exact digit
-  // slices (oz.cu); smaller ones cost less in the FP64 kernels than their slicing
+  // slices (oz.cu); smaller ones cost less in the FP64 kernels than their slicing.  A V C
+  // product pads its reduction width d to a 128-entry window, so it needs d >= 32.
   bool emulate(int64_t a, int64_t b) const {
-    return sizeof(T) == 8 && h_->opt.fp64_emulation && n_ >= 16384 && a * b >= 2048 && a >= 8 &&
+    return sizeof(T) == 8 && h_->opt.fp64_emulation && n_ >= 16384 && a * b >= 512 && a >= 8 &&
            b >= 8;
   }
   int gramT(int m, int k, double alpha, const T *X, int64_t ldx, const T *Y, int64_t ldy,
@@ -470,7 +471,7 @@ class Engine {
   int vcT(int d, int q, double alpha, const T *V, int64_t ldv, const double *C, int64_t ldc,
           double beta, T *Y, int64_t ldy) {
     const double vbytes = (double)n_ * (d + (beta != 0.0 ? 2 : 1) * q) * sizeof(T);
-    if (emulate(d, q)) {
+    if (d >= 32 && emulate(d, q)) {
       g_launches += 3;
       ProfScope ps(prof, GCGE_K_VC64TC, vbytes, 2.0 * n_ * d * q);
       return oz_vc(n_, d, q, alpha, (const double *)V, ldv, C, ldc, beta, (double *)Y, ldy, ws_,

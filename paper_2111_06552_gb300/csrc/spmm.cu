@@ -11,7 +11,7 @@
 // a whole row's worth of FMAs and keeps many independent gathers in flight; the
 // nonzero loop is unrolled by four.
 //
-// The rows are dealt to the CTAs in chunks of 8 CTA steps (256 / G rows per step), in
+// The rows are dealt to the CTAs in chunks of 2 CTA steps (256 / G rows per step), in
 // turn, two to four CTAs per SM: within a chunk consecutive rows of a banded (stencil /
 // FEM) matrix gather mostly the same rows of X, which stay in L1 between the CTA's
 // steps; across the grid all CTAs sweep the rows together, so the rows of X that are
@@ -241,7 +241,7 @@ Plan plan_for(int64_t n, int k, bool aligned) {
   const int64_t cap = (int64_t)device_sm_count() * (sizeof(T) == 4 ? 4 : 2);   // row streams per SM
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  const int64_t chunk = step * 8;   // rows per chunk: 8 CTA steps
+  const int64_t chunk = step * 2;   // rows per chunk: 2 CTA steps
   const int64_t nchunk = (n + chunk - 1) / chunk;
   if (grid > nchunk) grid = nchunk;
   if (grid < 1) grid = 1;
