@@ -138,10 +138,13 @@ gram64_partial_kernel(int64_t n, int m, int k, int TMx, int TKx, const double *_
       sy[rr][cc] = r < r1 ? Y[r * ldy + k0 + cc] : 0.0;
     }
     __syncthreads();
+    // warps whose outputs all lie beyond the tile issue no FMAs (the FP64 pipe is the
+    // bound, so padded outputs would cost as much as real ones)
 #pragma unroll 4
     for (int rr = 0; rr < GR; ++rr) {
 #pragma unroll
-      for (int i = 0; i < O; ++i) acc[i] += sx[rr][om[i]] * sy[rr][ok[i]];
+      for (int i = 0; i < O; ++i)
+        if ((int)(threadIdx.x & ~31u) + 256 * i < nout) acc[i] += sx[rr][om[i]] * sy[rr][ok[i]];
     }
     __syncthreads();
   }
@@ -234,6 +237,84 @@ vc_kernel(int64_t n, int d, int q, T alpha, const T *__restrict__ V, int64_t ldv
         *yp = out;
       }
     }
+  }
+}
+
+// FP64 V C with exact-fit tiles: a CTA takes VFR rows and TQx <= 32 columns of Y
+// (TQx chosen per call to cover q with little padding); output o = t + 256 i sits at
+// row o / qt, column o % qt of the tile, so every lane of a live warp holds a real
+// output and warps past the tile issue no FMAs.  The reduction over d runs in stages
+// of VD columns of V.
+constexpr int VFR = 128;
+
+template <int O>
+__global__ void __launch_bounds__(256)
+vc64_fit_kernel(int64_t n, int d, int q, int TQx, double alpha, const double *__restrict__ V,
+                int64_t ldv, const double *__restrict__ C, int64_t ldc, double beta,
+                double *__restrict__ Y, int64_t ldy) {
+  __shared__ double sv[VFR][VD + 1];
+  __shared__ double sc[VD][33];
+  const int64_t rbase = (int64_t)blockIdx.x * VFR;
+  const int q0 = blockIdx.y * TQx;
+  const int qt = (q - q0) < TQx ? (q - q0) : TQx;
+  const int nout = VFR * qt;
+  const int wbase = (int)(threadIdx.x & ~31u);
+  int orow[O], oj[O];
+  double acc[O];
+#pragma unroll
+  for (int i = 0; i < O; ++i) {
+    const int o = threadIdx.x + 256 * i;
+    orow[i] = o < nout ? o / qt : 0;
+    oj[i] = o < nout ? o % qt : 0;
+    acc[i] = 0.0;
+  }
+  for (int d0 = 0; d0 < d; d0 += VD) {
+    const int dt = (d - d0) < VD ? (d - d0) : VD;
+    for (int u = threadIdx.x; u < VFR * dt; u += 256) {
+      const int rr = u / dt, cc = u % dt;
+      const int64_t r = rbase + rr;
+      sv[rr][cc] = r < n ? V[r * ldv + d0 + cc] : 0.0;
+    }
+    for (int u = threadIdx.x; u < dt * qt; u += 256) {
+      const int rr = u / qt, cc = u % qt;
+      sc[rr][cc] = C[(d0 + rr) + (int64_t)(q0 + cc) * ldc];
+    }
+    __syncthreads();
+    for (int e = 0; e < dt; ++e) {
+#pragma unroll
+      for (int i = 0; i < O; ++i)
+        if (wbase + 256 * i < nout) acc[i] = fma(sv[orow[i]][e], sc[e][oj[i]], acc[i]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < O; ++i) {
+    const int o = threadIdx.x + 256 * i;
+    const int64_t r = rbase + orow[i];
+    if (o < nout && r < n) {
+      double *yp = Y + r * ldy + q0 + oj[i];
+      double out = alpha * acc[i];
+      if (beta != 0.0) out += beta * *yp;
+      *yp = out;
+    }
+  }
+}
+
+void launch_vc64(int64_t n, int d, int q, double alpha, const double *V, int64_t ldv,
+                 const double *C, int64_t ldc, double beta, double *Y, int64_t ldy,
+                 cudaStream_t st) {
+  const int tq = ceil_div(q, 32);
+  const int TQx = ceil_div(q, tq);
+  const int O = (VFR * TQx + 255) / 256;
+  dim3 grid((unsigned)ceil_div(n, VFR), (unsigned)tq);
+  switch (O) {
+#define GCGE_V64(o) \
+    case o: vc64_fit_kernel<o><<<grid, 256, 0, st>>>(n, d, q, TQx, alpha, V, ldv, C, ldc, beta, Y, ldy); break;
+    GCGE_V64(1) GCGE_V64(2) GCGE_V64(3) GCGE_V64(4) GCGE_V64(5) GCGE_V64(6) GCGE_V64(7)
+    GCGE_V64(8) GCGE_V64(9) GCGE_V64(10) GCGE_V64(11) GCGE_V64(12) GCGE_V64(13) GCGE_V64(14)
+    GCGE_V64(15)
+    default: vc64_fit_kernel<16><<<grid, 256, 0, st>>>(n, d, q, TQx, alpha, V, ldv, C, ldc, beta, Y, ldy);
+#undef GCGE_V64
   }
 }
 
@@ -563,8 +644,12 @@ int vc(int64_t n, int d, int q, double alpha, const T *V, int64_t ldv, const dou
   if (n <= 0 || q <= 0) return GCGE_OK;
   if (d < 0) return GCGE_EINVAL;   // d == 0 leaves Y = beta * Y
   if (tc) return vc_tc<T>(n, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, st, ws);
-  dim3 grid((unsigned)ceil_div(n, VR), (unsigned)ceil_div(q, VQ));
-  vc_kernel<T><<<grid, 256, 0, st>>>(n, d, q, (T)alpha, V, ldv, C, ldc, (T)beta, Y, ldy);
+  if (sizeof(T) == 8) {
+    launch_vc64(n, d, q, alpha, (const double *)V, ldv, C, ldc, beta, (double *)Y, ldy, st);
+  } else {
+    dim3 grid((unsigned)ceil_div(n, VR), (unsigned)ceil_div(q, VQ));
+    vc_kernel<T><<<grid, 256, 0, st>>>(n, d, q, (T)alpha, V, ldv, C, ldc, (T)beta, Y, ldy);
+  }
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }

@@ -83,7 +83,8 @@ def test_spmm_f32_matches_oracle(g, k):
 
 
 @pytest.mark.parametrize("n,m,k", [(1, 1, 1), (1000, 7, 5), (4133, 70, 20), (20011, 150, 33),
-                                   (3001, 200, 100)])
+                                   (3001, 200, 100), (20000, 10, 10), (5003, 20, 20),
+                                   (3000, 13, 9)])
 def test_gram_f64_into_strided_subblock(g, n, m, k):
     import torch
     rng = np.random.default_rng(n + m)
@@ -118,7 +119,9 @@ def test_gram_f32(g, n, m, k, tc):
     assert np.all(np.abs(host(Cd).T - ref) <= 2e-6 * bound)
 
 
-@pytest.mark.parametrize("n,d,q", [(1, 1, 1), (999, 13, 7), (10007, 200, 180), (4096, 70, 50)])
+@pytest.mark.parametrize("n,d,q", [(1, 1, 1), (999, 13, 7), (10007, 200, 180), (4096, 70, 50),
+                                   (20000, 10, 10), (385, 20, 20), (5000, 33, 65),
+                                   (777, 17, 31), (1000, 0, 3)])
 def test_vc_f64(g, n, d, q):
     import torch
     rng = np.random.default_rng(d)
@@ -132,7 +135,9 @@ def test_vc_f64(g, n, d, q):
     g.gcge_vc_f64(n, d, q, -1.0, dev(padded(V, ldv)), ldv, dev(Cbuf), ldc, 2.0, Yd, ldy)
     torch.cuda.synchronize()
     ref = -(V @ Cm) + 2.0 * Y0
-    assert np.abs(host(Yd)[:, :q] - ref).max() <= 1e-12 * (np.abs(ref).max() + 1)
+    got = host(Yd)
+    assert np.abs(got[:, :q] - ref).max() <= 1e-12 * (np.abs(ref).max() + 1)
+    assert np.all(np.isnan(got[:, q:]))             # padding columns untouched
 
 
 @pytest.mark.parametrize("tc", [0, 1])
