@@ -9,15 +9,17 @@
 //    128 entries.  Within a window every row of an operand gets one exponent E with
 //    max|x| < 2^E; x / 2^E is rounded to 49 fraction bits and written as seven
 //    signed 7-bit digits d_1..d_7 (x / 2^E = sum_p d_p 2^-7p, error <= 2^-50).  Digit p
-//    is stored as the bf16 number d_p 2^-7(p-1) (exact: at most 7 significant bits),
+//    is stored unscaled, as the bf16 number d_p (exact: at most 7 significant bits),
 //    one plane per digit, K-major.  The slicing works on the FP64 bit patterns with
-//    integer operations only.
+//    integer operations only.  The small operand (B: the columns of Y, or of C) is
+//    sliced into planes in global memory; the large one (A: the columns of X, or the
+//    rows of V) is sliced inside the product, from FP64 straight into shared memory,
+//    after a pre-pass that finds its window exponents.
 //  * Products.  The 28 plane pairs (i, j) with i + j <= 8 are multiplied with
 //    tcgen05.mma kind::f16 (bf16 in, FP32 accumulate).  A pair contributes at the
-//    scale 2^-7(i+j-2); the pairs of one scale accumulate in their own
-//    tensor-memory accumulator (seven of them), where every partial sum is an
-//    integer multiple of that scale below 2^24 in magnitude (128 rows x at most 7
-//    pairs x 127^2), so all seven sums are exact.  The dropped pairs (i + j >= 9)
+//    scale 2^-7(i+j); the pairs of one scale accumulate in their own tensor-memory
+//    accumulator (seven of them), where every partial sum is an integer below 2^24 in
+//    magnitude (128 rows x at most 7 pairs x 127^2), so all seven sums are exact.  The dropped pairs (i + j >= 9)
 //    and the digit truncation bound the error: about 2^-47 max|x| max|y| per term
 //    (window maxima), against about 2^-53 sqrt(n) Sum|x||y| for an FP64 dot
 //    product of n terms.
@@ -25,12 +27,11 @@
 //    turned into integers and combined exactly in int64, converted once, scaled by
 //    the window's 2^(E_x + E_y) and added to FP64 registers.
 //
-// Kernel roles (192 threads): warp 0 issues TMA copies of the seven planes of each
-// operand tile per stage of 32 reduction entries (64-byte rows, 64-byte swizzle);
-// warp 1 allocates tensor memory and issues the MMAs (one elected lane); warps 2-5
-// own the 128 accumulator lanes (drain and epilogue).  Every mbarrier wait is
-// bounded; a timeout sets the device error flag read by gcge_tc_status and the
-// solver.
+// Kernel roles (320 threads): warp 0 issues TMA copies of B's seven planes per stage of
+// 32 reduction entries (64-byte rows, 64-byte swizzle); warp 1 allocates tensor memory
+// and issues the MMAs (one elected lane); warps 2-9 slice A into the stage buffers and
+// drain the accumulators (epilogue included).  Every mbarrier wait is bounded; a
+// timeout sets the device error flag read by gcge_tc_status and the solver.
 #include <algorithm>
 
 #include "blas.cuh"
@@ -49,8 +50,7 @@ constexpr int kWin = 128;                  // reduction entries per exact window
 constexpr int kKS = 32;                    // reduction entries per stage (64-byte rows)
 constexpr int kStPerWin = kWin / kKS;      // stages per window
 constexpr int kGroups = 7;                 // accumulators: one per scale s = i + j = 0..6
-constexpr int kOzThreads = 192;
-constexpr int kStages = 2;
+constexpr int kMaxStages = 3;
 constexpr int kExpZero = -4000;            // exponent of an all-zero window row
 constexpr int kMaxN = 64;                  // output columns per CTA (7 x 64 TMEM columns)
 
@@ -63,17 +63,48 @@ constexpr int kSlSeg = kWin / 32;          // threads per row
 constexpr int kSlThreads = 256;
 static_assert(kSlRows * kSlSeg == kSlThreads, "one thread per 32 entries of a row");
 
-__device__ __forceinline__ uint16_t digit_bf16(uint32_t d, int p, uint32_t sign) {
-  if (d == 0) return 0;
-  const int h = 31 - __clz(d);                          // leading bit, 0..6
-  const uint32_t mant = (d << (7 - h)) & 0x7Fu;
-  const uint32_t ex = (uint32_t)(h - 7 * p + 127);
-  return (uint16_t)((sign << 15) | (ex << 7) | mant);
+// Digits are stored unscaled: plane p holds the signed integer d_p (|d_p| < 128) as a
+// bf16 number, exact with at most 7 significant bits.  float(d) is formed without a
+// conversion instruction (2^23 + d has d in its low mantissa bits), its low 16 bits are
+// zero, and the upper half of two such floats packs into one 32-bit word of two bf16.
+// The sign rides in the magic constant m = (-1)^s 2^23 (bit pattern 0x4B000000 with the
+// sign bit): float(m | d) - float(m) = (-1)^s (2^23 + d) - (-1)^s 2^23 = (-1)^s d, exact.
+__device__ __forceinline__ uint32_t digit_magic(unsigned long long u) {
+  return 0x4B000000u | ((uint32_t)(u >> 32) & 0x80000000u);
 }
 
+__device__ __forceinline__ uint32_t digit_f32(uint32_t d, uint32_t magic) {
+  return __float_as_uint(__uint_as_float(magic | d) - __uint_as_float(magic));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(uint32_t lo_f32, uint32_t hi_f32) {
+  return __byte_perm(lo_f32, hi_f32, 0x7632);
+}
+
+// Digit p (0-based, most significant first) of F < 2^49: bits [42 - 7p, 49 - 7p).
+// hi = F >> 21 holds digits 0-3, lo = F mod 2^21 digits 4-6 (32-bit shifts only).
+__device__ __forceinline__ uint32_t digit_of(uint32_t hi, uint32_t lo, int p) {
+  return p < 4 ? (hi >> (21 - 7 * p)) & 127u : (lo >> (14 - 7 * (p - 4))) & 127u;
+}
+
+// |x| / 2^Ex rounded to nearest at 49 fraction bits (kept below 2^49) from the FP64 bit
+// pattern u, for |x| < 2^Ex; zeros and subnormals give 0 (an all-zero row has only
+// those).  Branch-free: the shift is clamped to [4, 63] and the zero case selected.
+__device__ __forceinline__ unsigned long long frac49(unsigned long long u, int Ex) {
+  const int ex = (int)((u >> 52) & 0x7FF);
+  int sh = 1026 + Ex - ex;                            // >= 4 when ex != 0 (|x| < 2^Ex)
+  sh = sh < 4 ? 4 : (sh > 63 ? 63 : sh);
+  const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long f = (mant + (1ull << (sh - 1))) >> sh;
+  f = f > 0x1FFFFFFFFFFFFull ? 0x1FFFFFFFFFFFFull : f;
+  return ex == 0 ? 0ull : f;
+}
+
+// Rows i >= Iw (padding that no product tile reads) are neither sliced nor given an
+// exponent.
 __global__ void __launch_bounds__(kSlThreads)
 oz_slice_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, int64_t K,
-                int Rp, int64_t Kp, uint16_t *__restrict__ P, int *__restrict__ E) {
+                int Rp, int64_t Kp, int Iw, uint16_t *__restrict__ P, int *__restrict__ E) {
   extern __shared__ unsigned long long tile[];   // [kSlRows][kWin + 1] bit patterns
   const int i0 = blockIdx.y * kSlRows;
   const int64_t k0 = (int64_t)blockIdx.x * kWin;
@@ -109,25 +140,23 @@ oz_slice_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, i
   for (int q = 0; q < kSlSeg; ++q) mx = max(mx, smax[q][i]);
   const int exmax = (int)(mx >> 52);
   const int Ex = mx == 0 ? kExpZero : exmax - 1022;     // max < 2^Ex
+  if (i0 + i >= Iw) return;
   if (seg == 0) E[blockIdx.x * (int64_t)Rp + i0 + i] = Ex;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     unsigned long long F[16];   // |x| / 2^Ex in 49 fraction bits, 16 entries at a time
-    uint32_t signs = 0;
+    uint32_t magic[16];
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
       const unsigned long long u = row[16 * half + kk];
-      const int ex = (int)((u >> 52) & 0x7FF);
-      signs |= (uint32_t)(u >> 63) << kk;
-      unsigned long long f = 0;
-      if (ex != 0 && Ex != kExpZero) {
-        const int sh = 1026 + Ex - ex;                      // >= 4 since |x| < 2^Ex
-        const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        // rounded to nearest (no bias toward zero); the top value stays below 2^49
-        f = sh < 64 ? ((mant + (1ull << (sh - 1))) >> sh) : 0ull;
-        f = f > 0x1FFFFFFFFFFFFull ? 0x1FFFFFFFFFFFFull : f;
-      }
-      F[kk] = f;
+      magic[kk] = digit_magic(u);
+      F[kk] = frac49(u, Ex);
+    }
+    uint32_t fh[16], fl[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      fh[kk] = (uint32_t)(F[kk] >> 21);
+      fl[kk] = (uint32_t)F[kk] & 0x1FFFFFu;
     }
 #pragma unroll
     for (int p = 0; p < kDigits; ++p) {
@@ -139,14 +168,42 @@ oz_slice_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, i
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const int k1 = 8 * q + 2 * h, k2 = k1 + 1;
-          const uint32_t a = digit_bf16((uint32_t)(F[k1] >> (42 - 7 * p)) & 127u, p, (signs >> k1) & 1u);
-          const uint32_t b = digit_bf16((uint32_t)(F[k2] >> (42 - 7 * p)) & 127u, p, (signs >> k2) & 1u);
-          w[h] = a | (b << 16);
+          w[h] = pack_bf16x2(digit_f32(digit_of(fh[k1], fl[k1], p), magic[k1]),
+                             digit_f32(digit_of(fh[k2], fl[k2], p), magic[k2]));
         }
         dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
   }
+}
+
+// Window exponents of the operand sliced inside the product: E[w * Rp + i] = E with
+// max_k |A(i, k)| < 2^E over the window k in [128 w, 128 w + 128) (kExpZero for an
+// all-zero window row, and for the padding rows I <= i < Rp).  Element (i, k) is
+// src[i * si + k * sk]; one thread per row and window, the same rule as the slicer.
+__global__ void __launch_bounds__(256)
+oz_expo_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, int64_t K, int Rp,
+               int *__restrict__ E) {
+  const int64_t w = blockIdx.x;
+  const int i = blockIdx.y * 256 + threadIdx.x;
+  if (i >= Rp) return;
+  unsigned long long mx = 0;
+  if (i < I) {
+    const int64_t k0 = w * kWin;
+    const int64_t kn = (K - k0) < kWin ? (K - k0) : kWin;
+    const double *p = src + (int64_t)i * si + k0 * sk;
+    if (kn == kWin) {
+#pragma unroll 16
+      for (int k = 0; k < kWin; ++k)
+        mx = max(mx, (unsigned long long)__double_as_longlong(__ldg(p + k * sk)) &
+                         0x7FFFFFFFFFFFFFFFull);
+    } else {
+      for (int64_t k = 0; k < kn; ++k)
+        mx = max(mx, (unsigned long long)__double_as_longlong(__ldg(p + k * sk)) &
+                         0x7FFFFFFFFFFFFFFFull);
+    }
+  }
+  E[w * Rp + i] = mx == 0 ? kExpZero : (int)(mx >> 52) - 1022;
 }
 
 // ------------------------------------------------------------------------ products
@@ -179,34 +236,53 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// D(128 x N tile) = sum over the windows [w0, w1) of A_tile B_tile^T (both K-major
-// planes); out[i * so_i + j * so_j] = alpha D + beta out for i < mv, j < nv.
-__global__ void __launch_bounds__(kOzThreads, 1)
-oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const int *__restrict__ EA, int RpA, const int *__restrict__ EB, int RpB, int N,
-               int nwin, int wps, int mrow0, int mvalid, int nvalid, double alpha, double beta,
-               double *__restrict__ out, int64_t so_i, int64_t so_j, int64_t so_split,
-               int *__restrict__ err) {
+// ------------------------------------------------------------------------ fused product
+// The same product with the A operand sliced inside the kernel: A's FP64 entries are
+// read from global memory, cut into the seven digits below the window exponents EA
+// (computed by a pre-pass of oz_slice_kernel) and written straight into the stage's
+// plane buffers in the 64-byte-swizzle layout that the MMA descriptors expect (16-byte
+// unit c of row r at unit c ^ ((r >> 1) & 3)).  A's planes never reach global memory.
+// B's planes (the small operand) come by TMA as before.
+//   warp 0: TMA of B's planes; warp 1: MMA issuer;
+//   warps 2-9 (256 workers): slicing of A (thread = A-row, half of a 32-entry stage) and
+//   the window drain (thread = accumulator lane, half of the N columns).
+// A worker drains window w after slicing the first nst stages of window w + 1, so
+// the slicing of the next window overlaps the MMAs of the current one.
+constexpr int kFuThreads = 320;
+constexpr int kFuWorkers = 256;
+
+// NH: the most columns one worker drains (N / 2 <= NH); 16 for N <= 32 keeps the
+// accumulators and the prefetched loads in registers (10 warps allow 168 per thread).
+template <int NH>
+__global__ void __launch_bounds__(kFuThreads, 1)
+oz_fused_kernel(const __grid_constant__ CUtensorMap tmB, const double *__restrict__ A,
+                int64_t a_si, int64_t a_sk, int Arows, int64_t Klen, const int *__restrict__ EA,
+                int RpA, const int *__restrict__ EB, int RpB, int N, int nwin, int wps,
+                int mvalid, int nvalid, double alpha, double beta, double *__restrict__ out,
+                int64_t so_i, int64_t so_j, int64_t so_split, int nst, int *__restrict__ err) {
   extern __shared__ unsigned char smraw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], dfull, dfree, done;
+  __shared__ __align__(8) uint64_t fullb[kMaxStages], fulla[kMaxStages], empty[kMaxStages], dfull,
+      dfree, done;
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
   unsigned char *sm = smraw + ((1024u - (su32(smraw) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = blockIdx.y, nt = blockIdx.z;
   const int w0 = blockIdx.x * wps, w1 = min(nwin, w0 + wps);
-  const int nstage = (w1 - w0) * kStPerWin;
+  const int nw = max(0, w1 - w0);
+  const int nstage = nw * kStPerWin;
   const uint32_t abytes = (uint32_t)kDigits * 128 * 64, bbytes = (uint32_t)kDigits * N * 64;
   const uint32_t sbytes = (abytes + bbytes + 1023u) & ~1023u;
   const uint32_t ncols = 512;
   if (warp == 1) tmem_alloc(&tbase, ncols);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&fullb[s], 1);
+      mbar_init(&fulla[s], kFuWorkers);
       mbar_init(&empty[s], 1);
     }
     mbar_init(&dfull, 1);
-    mbar_init(&dfree, 128);
+    mbar_init(&dfree, kFuWorkers);
     mbar_init(&done, 1);
     abort_flag = 0;
     mbar_init_fence();
@@ -221,33 +297,30 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (lane == 0 && nstage > 0) {
       int issued = 0;
       for (int it = 0; it < nstage; ++it) {
-        const int s = it % kStages, u = it / kStages;
+        const int s = it % nst, u = it / nst;
         if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, err, ab)) break;
-        mbar_expect_tx(&full[s], abytes + bbytes);
+        mbar_expect_tx(&fullb[s], bbytes);
         const int k = (w0 * kStPerWin + it) * kKS;
-        tma_load_3d(sm + s * sbytes, &tmA, k, mt * 128 + mrow0, 0, &full[s]);
-        tma_load_3d(sm + s * sbytes + abytes, &tmB, k, nt * N, 0, &full[s]);
+        tma_load_3d(sm + s * sbytes + abytes, &tmB, k, nt * N, 0, &fullb[s]);
         ++issued;
       }
-      for (int it = max(0, issued - kStages); it < issued; ++it)
-        mbar_wait(&full[it % kStages], (it / kStages) & 1, err, nullptr);
+      for (int it = max(0, issued - nst); it < issued; ++it)
+        mbar_wait(&fullb[it % nst], (it / nst) & 1, err, nullptr);
     }
   } else if (warp == 1) {
     const bool leader = elect_one();
     const uint32_t id = idesc_bf16(128, N);
-    int it = 0;
-    for (; it < nstage; ++it) {
-      const int s = it % kStages, u = it / kStages;
+    for (int it = 0; it < nstage; ++it) {
+      const int s = it % nst, u = it / nst;
       const int wl = it % kStPerWin, wi = it / kStPerWin;
       if (wl == 0 && wi > 0 &&
           !__all_sync(0xFFFFFFFFu, mbar_wait(&dfree, (wi - 1) & 1, err, ab)))
         break;
-      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&full[s], u & 1, err, ab))) break;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&fulla[s], u & 1, err, ab))) break;
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&fullb[s], u & 1, err, ab))) break;
       tc_fence_after();
       const uint32_t abase = su32(sm + s * sbytes), bbase = abase + abytes;
       if (leader) {
-        // plane pairs (i, j), 0-based, s = i + j <= 6, into accumulator s; the first
-        // pair of an accumulator overwrites it at the start of a window
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
 #pragma unroll
@@ -276,33 +349,37 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     __syncwarp();
   } else {
-    // drain / epilogue: thread = accumulator lane (row of the 128 x N tile)
-    const int q = warp & 3;
-    const int row = 32 * q + lane;
+    const int wt = threadIdx.x - 64;
+    const int srow = wt & 127, shalf = wt >> 7;   // slicing: A-row, 16-entry half of a stage
+    const int ia_s = mt * 128 + srow;
+    const bool rvalid = ia_s < Arows;
+    const double *arow = A + (int64_t)ia_s * a_si;
+    const int q = warp & 3;                        // TMEM lane quadrant of this warp
+    const int ia_d = mt * 128 + 32 * q + lane;     // drain: accumulator lane = A-row
+    const int nh = N >> 1, c0 = ((warp - 2) >> 2) * nh;   // drain: this warp's column half
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
-    const int ia = mt * 128 + row;                 // row of A's planes (and of D)
-    double acc[kMaxN];
+    double acc[NH];
 #pragma unroll
-    for (int j = 0; j < kMaxN; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NH; ++j) acc[j] = 0.0;
     bool ok = true;
-    for (int wi = 0; wi < w1 - w0 && ok; ++wi) {
-      if (!mbar_wait(&dfull, wi & 1, err, ab)) { ok = false; break; }
+    int wd = 0;   // next window to drain
+    auto drain = [&](int wdi) -> bool {
+      if (!mbar_wait(&dfull, wdi & 1, err, ab)) return false;
       tc_fence_after();
-      const int w = w0 + wi;
-      const int ea = EA[(int64_t)w * RpA + mrow0 + ia];
-      const int *eb = EB + (int64_t)w * RpB + nt * N;
-      // accumulator s holds an exact multiple of 2^-7s (in units of the leading product
-      // 2^(Ex + Ey - 14)); I_s = acc_s 2^7s is an integer below 2^24.  The window sum in
-      // units of 2^-28: T = sum_{s<=4} I_s 2^(28-7s) + round((I_5 2^7 + I_6) / 2^14),
-      // exact in int64 up to that rounding (|T| < 2^50), then one conversion and one FMA.
+      const int w = w0 + wdi;
+      const int ea = EA[(int64_t)w * RpA + ia_d];
+      const int *eb = EB + (int64_t)w * RpB + nt * N + c0;
+      // accumulator s holds the integer I_s = sum over i + j = s of d_i d_j (|I_s| < 2^24,
+      // exact in FP32), in units of 2^(Ex + Ey - 14 - 7s).  The window sum in units of
+      // 2^-28 (of 2^(Ex + Ey - 14)): T = sum_{s<=4} I_s 2^(28-7s) + round((I_5 2^7 + I_6)
+      // / 2^14), exact in int64 up to that rounding (|T| < 2^50).
 #pragma unroll
-      for (int jb = 0; jb < kMaxN; jb += 8) {
-        if (jb < N) {
-          // the seven accumulators' 8 columns in one batch of loads, one wait
+      for (int jb = 0; jb < NH; jb += 8) {
+        if (jb < nh) {
           uint32_t gv[kGroups][8];
 #pragma unroll
           for (int sd = 0; sd < kGroups; ++sd) {
-            const uint32_t ta = tmem + lane_addr + sd * N + jb;
+            const uint32_t ta = tmem + lane_addr + sd * N + c0 + jb;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                 : "=r"(gv[sd][0]), "=r"(gv[sd][1]), "=r"(gv[sd][2]), "=r"(gv[sd][3]),
@@ -315,8 +392,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             long long T = 0, Lw = 0;
 #pragma unroll
             for (int sd = 0; sd < kGroups; ++sd) {
-              const float up = __int_as_float((127 + 7 * sd) << 23);   // 2^(7 sd)
-              const long long I = (long long)__float2int_rn(__uint_as_float(gv[sd][u]) * up);
+              const long long I = (long long)__float2int_rn(__uint_as_float(gv[sd][u]));
               if (sd <= 4) T += I << (28 - 7 * sd);
               else if (sd == 5) Lw = I << 7;
               else T += (Lw + I + (1ll << 13)) >> 14;   // rounded, not floored
@@ -327,12 +403,87 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
       tc_fence_before();
       mbar_arrive(&dfree);
-    }
-    if (ok && ia < mvalid) {
-      double *o = out + blockIdx.x * so_split + (int64_t)ia * so_i + (int64_t)nt * N * so_j;
+      return true;
+    };
+    // raw FP64 bits of this thread's 16 entries of stage it; the next stage's loads are
+    // issued before the current one is sliced, so their latency overlaps the work
+    unsigned long long raw[16];
+    auto load = [&](int it, unsigned long long (&dst)[16]) {
+      const int64_t k0 = (int64_t)(w0 * kStPerWin + it) * kKS + shalf * 16;
+      if (rvalid && k0 + 16 <= Klen) {
 #pragma unroll
-      for (int j = 0; j < kMaxN; ++j) {
-        if (j < N && nt * N + j < nvalid) {
+        for (int kk = 0; kk < 16; ++kk)
+          dst[kk] = (unsigned long long)__double_as_longlong(__ldg(arow + (k0 + kk) * a_sk));
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+          dst[kk] = (rvalid && k0 + kk < Klen)
+                        ? (unsigned long long)__double_as_longlong(__ldg(arow + (k0 + kk) * a_sk))
+                        : 0ull;
+      }
+    };
+    if (nstage > 0) load(0, raw);
+    for (int it = 0; it < nstage && ok; ++it) {
+      const int s = it % nst, u = it / nst;
+      // the window before this one is drained once the first nst stages of this one are
+      // sliced (slicing further would wait on MMAs that wait on that drain)
+      const bool drain_now = it == (wd + 1) * kStPerWin + nst - 1;
+      // cut the 16 entries into digits below this A-row's window exponent
+      const int Ex = EA[(int64_t)(w0 + it / kStPerWin) * RpA + ia_s];
+      uint32_t fh[16], fl[16];
+      uint32_t magic[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        magic[kk] = digit_magic(raw[kk]);
+        const unsigned long long F = frac49(raw[kk], Ex);
+        fh[kk] = (uint32_t)(F >> 21);
+        fl[kk] = (uint32_t)F & 0x1FFFFFu;
+      }
+      // the next stage's loads fly while this one is written (after the drain when there
+      // is one, which needs the registers)
+      if (!drain_now && it + 1 < nstage) load(it + 1, raw);
+      if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, err, ab)) {
+        ok = false;
+        break;
+      }
+      {
+        unsigned char *pa = sm + s * sbytes + srow * 64;
+        const int sw = (srow >> 1) & 3;
+#pragma unroll
+        for (int p = 0; p < kDigits; ++p) {
+#pragma unroll
+          for (int cq = 0; cq < 2; ++cq) {
+            uint32_t wv[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int k1 = 8 * cq + 2 * h, k2 = k1 + 1;
+              wv[h] = pack_bf16x2(digit_f32(digit_of(fh[k1], fl[k1], p), magic[k1]),
+                                  digit_f32(digit_of(fh[k2], fl[k2], p), magic[k2]));
+            }
+            const int unit = (2 * shalf + cq) ^ sw;
+            *reinterpret_cast<uint4 *>(pa + p * (128 * 64) + unit * 16) =
+                make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          }
+        }
+        fence_async_smem();   // generic-proxy stores -> visible to the tensor core
+        mbar_arrive(&fulla[s]);
+      }
+      if (drain_now) {
+        if (!drain(wd)) {
+          ok = false;
+          break;
+        }
+        ++wd;
+        if (it + 1 < nstage) load(it + 1, raw);
+      }
+    }
+    for (; ok && wd < nw; ++wd)
+      if (!drain(wd)) ok = false;
+    if (ok && ia_d < mvalid) {
+      double *o = out + blockIdx.x * so_split + (int64_t)ia_d * so_i + (int64_t)(nt * N + c0) * so_j;
+#pragma unroll
+      for (int j = 0; j < NH; ++j) {
+        if (j < nh && nt * N + c0 + j < nvalid) {
           double *oj = o + (int64_t)j * so_j;
           double v = alpha * acc[j];
           if (beta != 0.0) v += beta * *oj;
@@ -383,7 +534,7 @@ bool plane_map(CUtensorMap *map, const uint16_t *P, int Rp, int64_t Kp, int rows
 }
 
 int slice(const double *src, int64_t si, int64_t sk, int I, int64_t K, int Rp, int64_t Kp,
-          uint16_t *P, int *E, cudaStream_t st) {
+          int Iw, uint16_t *P, int *E, cudaStream_t st) {
   const size_t smem = (size_t)kSlRows * (kWin + 1) * 8;
   static bool attr = false;
   if (!attr) {
@@ -391,34 +542,59 @@ int slice(const double *src, int64_t si, int64_t sk, int I, int64_t K, int Rp, i
                                    (int)smem));
     attr = true;
   }
-  dim3 grid((unsigned)(Kp / kWin), (unsigned)(Rp / kSlRows));
-  oz_slice_kernel<<<grid, kSlThreads, smem, st>>>(src, si, sk, I, K, Rp, Kp, P, E);
+  dim3 grid((unsigned)(Kp / kWin), (unsigned)((Iw + kSlRows - 1) / kSlRows));
+  oz_slice_kernel<<<grid, kSlThreads, smem, st>>>(src, si, sk, I, K, Rp, Kp, Iw, P, E);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
 
-size_t gemm_smem(int N) {
-  const uint32_t sbytes = ((uint32_t)kDigits * (128 + N) * 64 + 1023u) & ~1023u;
-  return (size_t)kStages * sbytes + 1024;
+int expo(const double *src, int64_t si, int64_t sk, int I, int64_t K, int Rp, int nwin, int *E,
+         cudaStream_t st) {
+  dim3 grid((unsigned)nwin, (unsigned)((Rp + 255) / 256));
+  oz_expo_kernel<<<grid, 256, 0, st>>>(src, si, sk, I, K, Rp, E);
+  GCGE_LAUNCH_CHECK();
+  return GCGE_OK;
 }
 
-int gemm_launch(const CUtensorMap &ma, const CUtensorMap &mb, const int *EA, int RpA,
-                const int *EB, int RpB, int N, int nwin, int wps, int splits, int mtiles,
-                int ntiles, int mrow0, int mvalid, int nvalid, double alpha, double beta,
-                double *out, int64_t so_i, int64_t so_j, int64_t so_split, cudaStream_t st) {
+// Stages of the fused product: three when they fit in shared memory (N <= 32), else two.
+int fused_stages(int N) {
+  const uint32_t sbytes = ((uint32_t)kDigits * (128 + N) * 64 + 1023u) & ~1023u;
+  return (size_t)kMaxStages * sbytes + 1024 <= 227u * 1024 ? kMaxStages : 2;
+}
+
+size_t fused_smem(int N) {
+  const uint32_t sbytes = ((uint32_t)kDigits * (128 + N) * 64 + 1023u) & ~1023u;
+  return (size_t)fused_stages(N) * sbytes + 1024;
+}
+
+int fused_launch(const CUtensorMap &mb, const double *A, int64_t a_si, int64_t a_sk, int Arows,
+                 int64_t Klen, const int *EA, int RpA, const int *EB, int RpB, int N, int nwin,
+                 int wps, int splits, int mtiles, int ntiles, int mvalid, int nvalid, double alpha,
+                 double beta, double *out, int64_t so_i, int64_t so_j, int64_t so_split,
+                 cudaStream_t st) {
   int *err = nullptr;
   GCGE_CHECK(tc::err_flag(&err));
-  const size_t smem = gemm_smem(N);
-  static size_t attr = 0;
+  const size_t smem = fused_smem(N);
+  static size_t attr16 = 0, attr32 = 0;
+  size_t &attr = N <= 32 ? attr16 : attr32;
   if (smem > attr) {
-    GCGE_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+    if (N <= 32)
+      GCGE_CUDA(cudaFuncSetAttribute(oz_fused_kernel<16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
+      GCGE_CUDA(cudaFuncSetAttribute(oz_fused_kernel<kMaxN / 2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }
   dim3 grid((unsigned)splits, (unsigned)mtiles, (unsigned)ntiles);
-  oz_gemm_kernel<<<grid, kOzThreads, smem, st>>>(ma, mb, EA, RpA, EB, RpB, N, nwin, wps, mrow0,
-                                                 mvalid, nvalid, alpha, beta, out, so_i, so_j,
-                                                 so_split, err);
+  if (N <= 32)
+    oz_fused_kernel<16><<<grid, kFuThreads, smem, st>>>(
+        mb, A, a_si, a_sk, Arows, Klen, EA, RpA, EB, RpB, N, nwin, wps, mvalid, nvalid, alpha, beta,
+        out, so_i, so_j, so_split, fused_stages(N), err);
+  else
+    oz_fused_kernel<kMaxN / 2><<<grid, kFuThreads, smem, st>>>(
+        mb, A, a_si, a_sk, Arows, Klen, EA, RpA, EB, RpB, N, nwin, wps, mvalid, nvalid, alpha, beta,
+        out, so_i, so_j, so_split, fused_stages(N), err);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
@@ -457,46 +633,39 @@ int oz_gram(int64_t n, int m, int k, double alpha, const double *X, int64_t ldx,
   int N = 0, ntiles = 0;
   n_tiling(k, &N, &ntiles);
   const int RpB = (int)round_up((int64_t)ntiles * N, kSlRows);   // slicing works in row tiles
-  const int mtiles_all = (m + 127) / 128;
-  const int mchunk = std::min(mtiles_all, 4);
-  const int RpA = mchunk * 128;
-  const int64_t bytes_per_row = (int64_t)kDigits * 2 * (RpA + RpB);
+  const int mtiles = (m + 127) / 128;
+  const int RpA = mtiles * 128;
+  // per row of X/Y: Y's planes and the two exponent tables (one entry per window)
+  const int64_t bytes_per_row = (int64_t)kDigits * 2 * RpB + (4 * (int64_t)(RpA + RpB)) / kWin + 1;
   int64_t nc = std::max<int64_t>(kWin, (int64_t)(kPlaneBudget / bytes_per_row) / kWin * kWin);
   nc = std::min(nc, round_up(n, kWin));
   const int nwc = (int)(nc / kWin);                 // windows per row chunk
   const int sm_count = device_sm_count();
-  int splits = std::max(1, sm_count / std::max(1, mchunk * ntiles));
+  int splits = std::max(1, sm_count / std::max(1, mtiles * ntiles));
   splits = std::min(splits, nwc);
   const size_t bytes = (size_t)kDigits * RpB * nc * 2 + (size_t)nwc * RpB * 4 +
-                       (size_t)kDigits * RpA * nc * 2 + (size_t)nwc * RpA * 4 +
-                       (size_t)splits * m * k * 8 + 8 * 1024;
+                       (size_t)nwc * RpA * 4 + (size_t)splits * m * k * 8 + 8 * 1024;
   void *wsp = nullptr;
   GCGE_CHECK(ws.get(bytes, st, &wsp));
   Carve cv{static_cast<unsigned char *>(wsp)};
   uint16_t *PB = cv.take<uint16_t>((size_t)kDigits * RpB * nc);
   int *EBt = cv.take<int>((size_t)nwc * RpB);
-  uint16_t *PA = cv.take<uint16_t>((size_t)kDigits * RpA * nc);
   int *EAt = cv.take<int>((size_t)nwc * RpA);
   double *part = cv.take<double>((size_t)splits * m * k);
-  CUtensorMap mb, ma;
-  if (!plane_map(&mb, PB, RpB, nc, N) || !plane_map(&ma, PA, RpA, nc, 128)) return GCGE_EINVAL;
+  CUtensorMap mb;
+  if (!plane_map(&mb, PB, RpB, nc, N)) return GCGE_EINVAL;
   for (int64_t r0 = 0; r0 < n; r0 += nc) {
     const int64_t rows = std::min(nc, n - r0);
     const int nwin = (int)((rows + kWin - 1) / kWin);
     const int wps = (nwin + splits - 1) / splits;
-    const int used = (nwin + wps - 1) / wps;          // CTAs with windows; the rest add zero
-    (void)used;
     // Y: rows of the B planes are the columns of Y, reduction over the rows of Y
-    GCGE_CHECK(slice(Y + r0 * ldy, 1, ldy, k, rows, RpB, nc, PB, EBt, st));
-    for (int t0 = 0; t0 < mtiles_all; t0 += mchunk) {
-      const int tiles = std::min(mchunk, mtiles_all - t0);
-      const int c0 = t0 * 128, cols = std::min(m - c0, tiles * 128);
-      GCGE_CHECK(slice(X + r0 * ldx + c0, 1, ldx, cols, rows, RpA, nc, PA, EAt, st));
-      // part[split][j][c0 + i] += this chunk's share (overwritten by the first chunk)
-      GCGE_CHECK(gemm_launch(ma, mb, EAt, RpA, EBt, RpB, N, nwin, wps, splits, tiles, ntiles, 0,
-                             cols, k, 1.0, r0 == 0 ? 0.0 : 1.0, part + c0, 1, m, (int64_t)m * k,
-                             st));
-    }
+    GCGE_CHECK(slice(Y + r0 * ldy, 1, ldy, k, rows, RpB, nc, ntiles * N, PB, EBt, st));
+    // X: only the window exponents; the digits are cut inside the product
+    GCGE_CHECK(expo(X + r0 * ldx, 1, ldx, m, rows, RpA, nwin, EAt, st));
+    // part[split][j][i] += this chunk's share (overwritten by the first chunk)
+    GCGE_CHECK(fused_launch(mb, X + r0 * ldx, 1, ldx, m, rows, EAt, RpA, EBt, RpB, N, nwin, wps,
+                            splits, mtiles, ntiles, m, k, 1.0, r0 == 0 ? 0.0 : 1.0, part, 1, m,
+                            (int64_t)m * k, st));
   }
   return gram_reduce_launch(m, k, splits, part, alpha, beta, C, ldc, st);
 }
@@ -511,28 +680,29 @@ int oz_vc(int64_t n, int d, int q, double alpha, const double *V, int64_t ldv, c
   int N = 0, ntiles = 0;
   n_tiling(q, &N, &ntiles);
   const int RpB = (int)round_up((int64_t)ntiles * N, kSlRows);   // slicing works in row tiles
-  const size_t per_row = (size_t)kDigits * Kp * 2;
-  int64_t rchunk = (int64_t)std::max<size_t>(128, kPlaneBudget / per_row);
+  // the rows of V are taken in chunks only to bound the exponent table (one int per row
+  // and window); V's digits are cut inside the product
+  int64_t rchunk = (int64_t)std::max<size_t>(128, kPlaneBudget / ((size_t)nwin * 4));
   rchunk = std::min<int64_t>(round_up(n, 128), (rchunk / 128) * 128);
   const int RpA = (int)rchunk;
   const size_t bytes = (size_t)kDigits * RpB * Kp * 2 + (size_t)nwin * RpB * 4 +
-                       (size_t)kDigits * RpA * Kp * 2 + (size_t)nwin * RpA * 4 + 8 * 1024;
+                       (size_t)nwin * RpA * 4 + 8 * 1024;
   void *wsp = nullptr;
   GCGE_CHECK(ws.get(bytes, st, &wsp));
   Carve cv{static_cast<unsigned char *>(wsp)};
   uint16_t *PB = cv.take<uint16_t>((size_t)kDigits * RpB * Kp);
   int *EBt = cv.take<int>((size_t)nwin * RpB);
-  uint16_t *PA = cv.take<uint16_t>((size_t)kDigits * RpA * Kp);
   int *EAt = cv.take<int>((size_t)nwin * RpA);
   // C: rows of the B planes are the columns of C, reduction over the rows of C
-  GCGE_CHECK(slice(C, ldc, 1, q, d, RpB, Kp, PB, EBt, st));
-  CUtensorMap mb, ma;
-  if (!plane_map(&mb, PB, RpB, Kp, N) || !plane_map(&ma, PA, RpA, Kp, 128)) return GCGE_EINVAL;
+  GCGE_CHECK(slice(C, ldc, 1, q, d, RpB, Kp, ntiles * N, PB, EBt, st));
+  CUtensorMap mb;
+  if (!plane_map(&mb, PB, RpB, Kp, N)) return GCGE_EINVAL;
   for (int64_t r0 = 0; r0 < n; r0 += rchunk) {
     const int rows = (int)std::min<int64_t>(rchunk, n - r0);
-    GCGE_CHECK(slice(V + r0 * ldv, ldv, 1, rows, d, RpA, Kp, PA, EAt, st));
-    GCGE_CHECK(gemm_launch(ma, mb, EAt, RpA, EBt, RpB, N, nwin, nwin, 1, (rows + 127) / 128,
-                           ntiles, 0, rows, q, alpha, beta, Y + r0 * ldy, ldy, 1, 0, st));
+    GCGE_CHECK(expo(V + r0 * ldv, ldv, 1, rows, d, RpA, nwin, EAt, st));
+    GCGE_CHECK(fused_launch(mb, V + r0 * ldv, ldv, 1, rows, d, EAt, RpA, EBt, RpB, N, nwin, nwin,
+                            1, (rows + 127) / 128, ntiles, rows, q, alpha, beta, Y + r0 * ldy, ldy,
+                            1, 0, st));
   }
   return GCGE_OK;
 }
