@@ -319,33 +319,46 @@ void launch_vc64(int64_t n, int d, int q, double alpha, const double *V, int64_t
 }
 
 // ------------------------------------------------------------------ small FP64 GEMM
-__global__ void dgemm_small_kernel(int ta, int tb, int m, int n, int k, double alpha,
-                                   const double *__restrict__ A, int64_t lda,
-                                   const double *__restrict__ B, int64_t ldb, double beta,
-                                   double *__restrict__ C, int64_t ldc) {
-  __shared__ double sa[16][17];
-  __shared__ double sb[16][17];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+// C = alpha op(A) op(B) + beta C for the small dense FP64 products (Rayleigh-Ritz
+// matrices): 8 x 8 output tiles (64 threads, one output each) so that a d x d product
+// spreads over many more CTAs than SMs (the FP64 units are the limit), and the reduction
+// dimension staged 64 deep so that a CTA waits on memory only every 64 FMAs.
+constexpr int DT = 8, DK = 64;
+
+__global__ void __launch_bounds__(DT * DT)
+dgemm_small_kernel(int ta, int tb, int m, int n, int k, double alpha,
+                   const double *__restrict__ A, int64_t lda, const double *__restrict__ B,
+                   int64_t ldb, double beta, double *__restrict__ C, int64_t ldc) {
+  __shared__ double sa[DT][DK + 1];   // sa[i][p] = op(A)(i0 + i, p0 + p)
+  __shared__ double sb[DK][DT + 1];   // sb[p][j] = op(B)(p0 + p, j0 + j)
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * DT + tx;
+  const int i0 = blockIdx.x * DT, j0 = blockIdx.y * DT;
   double acc = 0.0;
-  for (int p0 = 0; p0 < k; p0 += 16) {
-    {  // A tile: rows blockIdx.x*16 + tx, cols p0 + ty
-      const int ii = blockIdx.x * 16 + tx, pp = p0 + ty;
-      double v = 0.0;
-      if (ii < m && pp < k) v = ta ? A[pp + (int64_t)ii * lda] : A[ii + (int64_t)pp * lda];
-      sa[tx][ty] = v;
-    }
-    {  // B tile: rows p0 + tx, cols blockIdx.y*16 + ty
-      const int pp = p0 + tx, jj = blockIdx.y * 16 + ty;
-      double v = 0.0;
-      if (pp < k && jj < n) v = tb ? B[jj + (int64_t)pp * ldb] : B[pp + (int64_t)jj * ldb];
-      sb[tx][ty] = v;
+  for (int p0 = 0; p0 < k; p0 += DK) {
+#pragma unroll
+    for (int u = 0; u < DT * DK / (DT * DT); ++u) {
+      const int e = t + u * DT * DT;        // 0 .. DT*DK-1
+      {  // op(A) tile: element (i, p), consecutive threads along the contiguous index
+        const int i = ta ? e / DK : e % DT, pp = ta ? e % DK : e / DT;
+        const int ii = i0 + i, kp = p0 + pp;
+        double v = 0.0;
+        if (ii < m && kp < k) v = ta ? A[kp + (int64_t)ii * lda] : A[ii + (int64_t)kp * lda];
+        sa[i][pp] = v;
+      }
+      {  // op(B) tile: element (p, j)
+        const int j = tb ? e % DT : e / DK, pp = tb ? e / DT : e % DK;
+        const int jj = j0 + j, kp = p0 + pp;
+        double v = 0.0;
+        if (kp < k && jj < n) v = tb ? B[jj + (int64_t)kp * ldb] : B[kp + (int64_t)jj * ldb];
+        sb[pp][j] = v;
+      }
     }
     __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) acc += sa[tx][e] * sb[e][ty];
+#pragma unroll 16
+    for (int e = 0; e < DK; ++e) acc = fma(sa[tx][e], sb[e][ty], acc);
     __syncthreads();
   }
+  const int i = i0 + tx, j = j0 + ty;
   if (i < m && j < n) {
     double *cp = C + i + (int64_t)j * ldc;
     double out = alpha * acc;
@@ -658,7 +671,7 @@ int dgemm_small(char ta, char tb, int m, int n, int k, double alpha, const doubl
                 const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
                 cudaStream_t st) {
   if (m <= 0 || n <= 0) return GCGE_OK;
-  dim3 grid(ceil_div(m, 16), ceil_div(n, 16)), block(16, 16);
+  dim3 grid(ceil_div(m, DT), ceil_div(n, DT)), block(DT, DT);
   dgemm_small_kernel<<<grid, block, 0, st>>>(ta == 'T', tb == 'T', m, n, k, alpha, A, lda, B, ldb,
                                              beta, C, ldc);
   GCGE_LAUNCH_CHECK();

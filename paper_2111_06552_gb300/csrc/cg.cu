@@ -166,6 +166,7 @@ cg_update_kernel(int64_t n, int k, const double *__restrict__ pq, const double *
 #pragma unroll
     for (int v = 0; v < VEC; ++v) al[v] = (T)(j0 + v < k ? salpha[j0 + v] : 0.0);
     const bool full = j0 + VEC <= k;
+#pragma unroll 2
     for (int64_t row = (int64_t)blockIdx.x * sl.rows_per_block + sl.row0; row < n;
          row += (int64_t)gridDim.x * sl.rows_per_block) {
       const T mi = minv ? minv[row] : T(1);
@@ -308,9 +309,9 @@ __global__ void jacobi_inverse_kernel(int64_t n, const int32_t *__restrict__ rp,
 int upd_grid(int64_t n, int k) {
   const int rpp = kCgThreads / (k < kCgThreads ? k : kCgThreads);
   int64_t g = (n + (int64_t)rpp * 4 - 1) / ((int64_t)rpp * 4);
-  // two CTAs per SM: enough to stream the vectors, and few partial rows for the
-  // last CTA to sum
-  const int64_t cap = (int64_t)device_sm_count() * 2;
+  // four CTAs per SM (with two rows in flight per thread in the update): enough loads
+  // in flight to stream the vectors, and few partial rows for the last CTA to sum
+  const int64_t cap = (int64_t)device_sm_count() * 4;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

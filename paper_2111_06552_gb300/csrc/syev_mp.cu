@@ -40,18 +40,22 @@ struct OjPlan {
   size_t smem;
 };
 
-// Cluster size C (power of two, 1..16) and block width b <= 32 such that three
-// buffers of (G, V) blocks of b columns x dp rows fit in shared memory.
+// Cluster size C (power of two, 1..16) and block width b such that three buffers of
+// (G, V) blocks of b columns x dp rows fit in shared memory.  b <= 16 is preferred: a
+// round of rotations streams its columns through shared memory, so spreading the blocks
+// over more CTAs (SMs) shortens a round; b <= 32 when 16 CTAs are not enough.
 bool oj_plan(int d, OjPlan &pl) {
-  const int dp = ((d + 31) / 32) * 32;
-  for (int C = 1; C <= 16; C <<= 1) {
-    const int b = (d + 2 * C - 1) / (2 * C);
-    if (b > 32) continue;
-    const size_t smem = sizeof(float) * 6 * (size_t)b * dp;
-    if (smem > 200 * 1024) continue;
-    const int bi = b + (b & 1);
-    pl = {C, b, dp, 32 * std::max(b, bi), smem};
-    return true;
+  const int dp = ((d + 127) / 128) * 128;   // a lane takes 4 consecutive rows per 128
+  for (int bmax : {16, 32}) {
+    for (int C = 1; C <= 16; C <<= 1) {
+      const int b = (d + 2 * C - 1) / (2 * C);
+      if (b > bmax) continue;
+      const size_t smem = sizeof(float) * 6 * (size_t)b * dp;
+      if (smem > 200 * 1024) continue;
+      const int bi = b + (b & 1);
+      pl = {C, b, dp, 32 * std::max(b, bi), smem};
+      return true;
+    }
   }
   return false;
 }
@@ -70,15 +74,19 @@ __device__ __forceinline__ void rr_pair(int B, int r, int k, int &p, int &q) {
   q = a < c ? c : a;
 }
 
-// One-sided rotation of the column pair (x, y) of G and V by one warp.
+// One-sided rotation of the column pair (x, y) of G and V by one warp; a lane takes rows
+// 4 lane + 128 i .. + 3 (16-byte shared-memory accesses; dp is a multiple of 128).
 __device__ __forceinline__ bool oj_rotate(float *gx, float *gy, float *vx, float *vy, int dp,
                                           int lane, float tol) {
+  float4 *gx4 = reinterpret_cast<float4 *>(gx), *gy4 = reinterpret_cast<float4 *>(gy);
+  float4 *vx4 = reinterpret_cast<float4 *>(vx), *vy4 = reinterpret_cast<float4 *>(vy);
+  const int nq = dp >> 7;
   float al = 0.f, be = 0.f, ga = 0.f;
-  for (int r = lane; r < dp; r += 32) {
-    const float x = gx[r], y = gy[r];
-    al = fmaf(x, x, al);
-    be = fmaf(y, y, be);
-    ga = fmaf(x, y, ga);
+  for (int i = 0; i < nq; ++i) {
+    const float4 x = gx4[lane + 32 * i], y = gy4[lane + 32 * i];
+    al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+    be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+    ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -87,23 +95,27 @@ __device__ __forceinline__ bool oj_rotate(float *gx, float *gy, float *vx, float
     ga += __shfl_xor_sync(0xffffffffu, ga, o);
   }
   if (al == 0.f || be == 0.f || !(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
-  const float ze = (be - al) / (2.f * ga);
-  const float t = (ze >= 0.f ? 1.f : -1.f) / (fabsf(ze) + sqrtf(1.f + ze * ze));
-  const float c = rsqrtf(1.f + t * t);
+  // tan of the rotation angle, the smaller root (fast reciprocal and square root: the
+  // rotation only has to be orthogonal to FP32 level, the FP64 stage refines it)
+  const float ze = __fdividef(be - al, 2.f * ga);
+  const float h = fmaf(ze, ze, 1.f);
+  const float t = __fdividef(ze >= 0.f ? 1.f : -1.f, fabsf(ze) + h * rsqrtf(h));
+  const float c = rsqrtf(fmaf(t, t, 1.f));
   const float s = c * t;
-  for (int r = lane; r < dp; r += 32) {
-    const float x = gx[r], y = gy[r];
-    gx[r] = c * x - s * y;
-    gy[r] = s * x + c * y;
-    const float u = vx[r], w = vy[r];
-    vx[r] = c * u - s * w;
-    vy[r] = s * u + c * w;
+  for (int i = 0; i < nq; ++i) {
+    const int r = lane + 32 * i;
+    const float4 x = gx4[r], y = gy4[r], u = vx4[r], w = vy4[r];
+    gx4[r] = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+    gy4[r] = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
+    vx4[r] = make_float4(c * u.x - s * w.x, c * u.y - s * w.y, c * u.z - s * w.z, c * u.w - s * w.w);
+    vy4[r] = make_float4(s * u.x + c * w.x, s * u.y + c * w.y, s * u.z + c * w.z, s * u.w + c * w.w);
   }
   return true;
 }
 
 __global__ void oj_cluster_kernel(int d, int b, int dp, const double *__restrict__ A, int64_t lda,
-                                  double sigma, float *__restrict__ Vout, int64_t ldv,
+                                  const double *__restrict__ gersh, float *__restrict__ Vout,
+                                  int64_t ldv,
                                   float *__restrict__ gnorm, int *__restrict__ flags,
                                   int max_sweeps) {
   extern __shared__ float4 smem4[];
@@ -130,6 +142,8 @@ __global__ void oj_cluster_kernel(int d, int b, int dp, const double *__restrict
     stop = 0;
   }
   __syncthreads();
+  // sigma: make G = A + sigma I positive semidefinite (Gershgorin lower bound)
+  const double sigma = gersh[0] < 0.0 ? -gersh[0] : 0.0;
   for (int s = 0; s < 2; ++s) {
     const int j0 = blk[s] * b;
     for (int u = threadIdx.x; u < b * dp; u += nthr) {
@@ -258,10 +272,16 @@ __global__ void gershgorin_kernel(int d, const double *__restrict__ A, int64_t l
   __shared__ double red[256];
   double mn = 1e300;
   for (int i = threadIdx.x; i < d; i += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < d; ++j)
-      if (j != i) s += fabs(A[i + (int64_t)j * lda]);
-    mn = fmin(mn, A[i + (int64_t)i * lda] - s);
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = 0;
+    for (; j + 4 <= d; j += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s4[u] += fabs(A[i + (int64_t)(j + u) * lda]);
+    }
+    for (; j < d; ++j) s4[0] += fabs(A[i + (int64_t)j * lda]);
+    const double aii = A[i + (int64_t)i * lda];
+    const double s = (s4[0] + s4[1]) + (s4[2] + s4[3]) - fabs(aii);
+    mn = fmin(mn, aii - s);
   }
   red[threadIdx.x] = mn;
   __syncthreads();
@@ -296,6 +316,7 @@ __global__ void ns_factor_kernel(int d, double *__restrict__ M, int64_t ld) {
 }
 
 constexpr int kMaxCluster = 32;
+constexpr int kMaxAnalyze = 1024;   // largest d of this method (16 CTAs x 2 blocks x 32)
 
 // Analysis of B (single CTA): lam = diag(B), the largest off-diagonal, clusters of the
 // sorted lam with gaps <= 100 * max_off.  Outputs: cid[d] cluster id per column,
@@ -307,6 +328,8 @@ __global__ void analyze_kernel(int d, const double *__restrict__ B, int64_t ldb,
                                int *__restrict__ cstart, int *__restrict__ info,
                                double *__restrict__ dinfo) {
   __shared__ double red[1024];
+  __shared__ double slam[kMaxAnalyze];
+  __shared__ int sord[kMaxAnalyze];
   __shared__ double s_off;
   double mx = 0.0, ml = 0.0;
   for (int64_t t = threadIdx.x; t < (int64_t)d * d; t += blockDim.x) {
@@ -328,27 +351,36 @@ __global__ void analyze_kernel(int d, const double *__restrict__ B, int64_t ldb,
     if (threadIdx.x == 0 && pass == 0) s_off = red[0];
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < d; i += blockDim.x) lam[i] = B[i + (int64_t)i * ldb];
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double v = B[i + (int64_t)i * ldb];
+    lam[i] = v;
+    slam[i] = v;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < d; i += blockDim.x) {
-    const double li = lam[i];
+    const double li = slam[i];
     int rank = 0;
-    for (int j = 0; j < d; ++j) rank += (lam[j] < li) || (lam[j] == li && j < i);
+    for (int j = 0; j < d; ++j) rank += (slam[j] < li) || (slam[j] == li && j < i);
     order[rank] = i;
+    sord[rank] = i;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     const double thr = 100.0 * s_off;
     int ncl = 0, big = 0, start = 0;
+    double prev = slam[sord[0]];
     for (int t = 0; t < d; ++t) {
-      if (t > 0 && lam[order[t]] - lam[order[t - 1]] > thr) {
+      const int o = sord[t];
+      const double cur = slam[o];
+      if (t > 0 && cur - prev > thr) {
         cstart[ncl] = start;
         big = max(big, t - start);
         ++ncl;
         start = t;
       }
-      cid[order[t]] = ncl;
-      clist[t] = order[t];
+      prev = cur;
+      cid[o] = ncl;
+      clist[t] = o;
     }
     cstart[ncl] = start;
     big = max(big, d - start);
@@ -555,11 +587,9 @@ int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_
   if (d < 2 || !oj_plan(d, pl)) return GCGE_EINVAL;
   GCGE_CHECK(mw.alloc(d));
   // sigma: make G = A + sigma I positive semidefinite
-  gershgorin_kernel<<<1, 256, 0, st>>>(d, A, lda, mw.dinfo);
+  if (d > kMaxAnalyze) return GCGE_EINVAL;
+  gershgorin_kernel<<<1, 256, 0, st>>>(d, A, lda, mw.dinfo + 4);   // read by the FP32 stage
   GCGE_LAUNCH_CHECK();
-  GCGE_CUDA(cudaMemcpyAsync(mw.h, mw.dinfo, sizeof(double), cudaMemcpyDeviceToHost, st));
-  GCGE_CUDA(cudaStreamSynchronize(st));
-  const double sigma = mw.h[0] < 0.0 ? -mw.h[0] : 0.0;
   // 1. FP32 one-sided block Jacobi in one cluster
   static bool attr_set = false;
   if (!attr_set) {
@@ -583,7 +613,8 @@ int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_
     cfg.numAttrs = 1;
     int64_t ld32 = d;
     int ms = 40;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, oj_cluster_kernel, d, pl.b, pl.dp, A, lda, sigma,
+    const double *gersh = mw.dinfo + 4;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, oj_cluster_kernel, d, pl.b, pl.dp, A, lda, gersh,
                                        mw.V32, ld32, mw.gn, flags_dev, ms);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
