@@ -169,21 +169,38 @@ void launch_gram64(dim3 grid, cudaStream_t st, int64_t n, int m, int k, int TMx,
   }
 }
 
-__global__ void gram_reduce_kernel(int m, int k, int splits, const double *__restrict__ part,
-                                   double alpha, double beta, double *__restrict__ C,
-                                   int64_t ldc) {
+// C(i, j) = alpha sum_sp part[sp][t] + beta C(i, j), t = i + m j.  A CTA takes 32
+// consecutive outputs (coalesced across the lanes) and 32 groups of splits: warp g sums
+// the splits g, g + 32, ... in order, and the 32 group sums are added in group order,
+// so the result is fixed for a given split count while many loads are in flight (a
+// Gram with few outputs and hundreds of splits no longer waits on one serial chain).
+constexpr int kRedGroups = 32;
+
+__global__ void __launch_bounds__(32 * kRedGroups)
+gram_reduce_kernel(int m, int k, int splits, const double *__restrict__ part, double alpha,
+                   double beta, double *__restrict__ C, int64_t ldc) {
+  __shared__ double sh[kRedGroups][33];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int64_t mk = (int64_t)m * k;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < mk;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int sp = 0; sp < splits; ++sp) s += part[(int64_t)sp * mk + t];
+  const int64_t t = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (t < mk)
+    for (int sp = g; sp < splits; sp += kRedGroups) s += part[(int64_t)sp * mk + t];
+  sh[g][lane] = s;
+  __syncthreads();
+  if (g == 0 && t < mk) {
+    double tot = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < kRedGroups; ++q) tot += sh[q][lane];
     const int i = (int)(t % m), j = (int)(t / m);
     double *cp = C + i + (int64_t)j * ldc;
-    double out = alpha * s;
+    double out = alpha * tot;
     if (beta != 0.0) out += beta * *cp;
     *cp = out;
   }
 }
+
+int red_blocks(int64_t mk) { return (int)((mk + 31) / 32); }
 
 // ------------------------------------------------------------------ V C
 constexpr int VR = 64, VQ = 32, VD = 16;
@@ -570,8 +587,8 @@ int gram_tc(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, cons
 
 int gram_reduce_launch(int m, int k, int splits, const double *part, double alpha, double beta,
                        double *C, int64_t ldc, cudaStream_t st) {
-  gram_reduce_kernel<<<elem_grid((int64_t)m * k), 256, 0, st>>>(m, k, splits, part, alpha, beta, C,
-                                                                 ldc);
+  gram_reduce_kernel<<<red_blocks((int64_t)m * k), 32 * kRedGroups, 0, st>>>(m, k, splits, part,
+                                                                            alpha, beta, C, ldc);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
@@ -610,7 +627,7 @@ int gram(int64_t n, int m, int k, double alpha, const T *X, int64_t ldx, const T
     GCGE_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * m * k, st));
     splits = 1;
   }
-  gram_reduce_kernel<<<elem_grid((int64_t)m * k), 256, 0, st>>>(m, k, (int)splits, part, alpha,
+  gram_reduce_kernel<<<red_blocks((int64_t)m * k), 32 * kRedGroups, 0, st>>>(m, k, (int)splits, part, alpha,
                                                                  beta, C, ldc);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
@@ -642,7 +659,8 @@ int gram_f64_workspace(int64_t n, int m, int k, double alpha, const double *X, i
     // nothing to reduce: the used partial block must read as zero
     GCGE_CUDA(cudaMemsetAsync(ws, 0, sizeof(double) * mk, st));
   }
-  gram_reduce_kernel<<<elem_grid(mk), 256, 0, st>>>(m, k, (int)splits, ws, alpha, beta, C, ldc);
+  gram_reduce_kernel<<<red_blocks(mk), 32 * kRedGroups, 0, st>>>(m, k, (int)splits, ws, alpha, beta,
+                                                                 C, ldc);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }

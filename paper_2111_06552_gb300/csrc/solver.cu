@@ -479,7 +479,9 @@ class Engine {
     }
     g_launches += 1;
     ProfScope ps(prof, cls(GCGE_K_VC), vbytes, 2.0 * n_ * d * q);
-    return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc(), st_, &ws_);
+    // reduction widths up to 32 (Algorithm 3 leaves, short deflations) stream faster
+    // through the SIMT kernel than through the tensor-core pipeline
+    return vc<T>(n_, d, q, alpha, V, ldv, C, ldc, beta, Y, ldy, use_tc() && d > 32, st_, &ws_);
   }
   int copyT(int k, const T *X, int64_t ldx, T *Y, int64_t ldy) {
     g_launches += 1;
