@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-largest", action="store_true")
     ap.add_argument("--table", action="store_true",
                     help="one mixed and one FP64 solve of every workload, one JSON line each")
+    ap.add_argument("--workloads", default=None,
+                    help="comma-separated workload names for --table (default: all)")
     ap.add_argument("--ablation", action="store_true",
                     help="shift / CG-step / orthogonaliser / preconditioner studies")
     ap.add_argument("--kernel-case", default=None,
@@ -504,13 +506,17 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ per-config table
-def run_table():
-    """One mixed and one FP64 solve (after one warm-up each) of every workload."""
+TABLE_WORKLOADS = ("fd2d_64", "q1_64", "fd3d_128", "q1grad_48", "rand_200k", "q1_160")
+
+
+def run_table(names=None):
+    """One mixed and one FP64 solve (after one warm-up each, none for the 160^3 pencil)
+    of every workload (or of those named)."""
     import torch
     import paper_2111_06552_gb300 as g
     g.lib()
     stream = torch.cuda.current_stream()
-    for name in ("fd2d_64", "q1_64", "fd3d_128", "q1grad_48", "rand_200k", "q1_160"):
+    for name in names or TABLE_WORKLOADS:
         p, nev, bs = workload(name)
         for prec, tag in ((g.GCGE_MIXED, "mixed"), (g.GCGE_FP64, "fp64")):
             s = g.Solver(p.A, p.B, nev, bs, 1e-8, precision=prec, seed=0, profile=1)
@@ -646,7 +652,11 @@ def main():
         kernel_case(args)
         return
     if args.table:
-        run_table()
+        names = [w for w in args.workloads.split(",") if w] if args.workloads else None
+        for w in names or ():
+            if w not in TABLE_WORKLOADS:
+                raise SystemExit(f"unknown workload {w!r}; choose from {TABLE_WORKLOADS}")
+        run_table(names)
         return
     if args.ablation:
         run_ablation()
