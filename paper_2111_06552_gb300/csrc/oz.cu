@@ -87,6 +87,11 @@ __device__ __forceinline__ uint32_t digit_of(uint32_t hi, uint32_t lo, int p) {
   return p < 4 ? (hi >> (21 - 7 * p)) & 127u : (lo >> (14 - 7 * (p - 4))) & 127u;
 }
 
+// High 32 bits of |x| (exponent field and top mantissa bits).
+__device__ __forceinline__ uint32_t hi_abs(double x) {
+  return (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
+}
+
 // |x| / 2^Ex rounded to nearest at 49 fraction bits (kept below 2^49) from the FP64 bit
 // pattern u, for |x| < 2^Ex; zeros and subnormals give 0 (an all-zero row has only
 // those).  Branch-free: the shift is clamped to [4, 63] and the zero case selected.
@@ -130,16 +135,16 @@ oz_slice_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, i
   // the tile (odd row stride) and the segment maxima combined through shared memory
   const int i = t % kSlRows, seg = t / kSlRows;
   const unsigned long long *row = tile + i * LD + seg * 32;
-  unsigned long long mx = 0;
+  uint32_t mx = 0;   // largest high word (sign cleared): its exponent field is the max
 #pragma unroll 8
-  for (int kk = 0; kk < 32; ++kk) mx = max(mx, row[kk] & 0x7FFFFFFFFFFFFFFFull);
-  __shared__ unsigned long long smax[kSlSeg][kSlRows];
+  for (int kk = 0; kk < 32; ++kk) mx = max(mx, (uint32_t)(row[kk] >> 32) & 0x7FFFFFFFu);
+  __shared__ uint32_t smax[kSlSeg][kSlRows];
   smax[seg][i] = mx;
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < kSlSeg; ++q) mx = max(mx, smax[q][i]);
-  const int exmax = (int)(mx >> 52);
-  const int Ex = mx == 0 ? kExpZero : exmax - 1022;     // max < 2^Ex
+  const int exmax = (int)(mx >> 20);
+  const int Ex = exmax == 0 ? kExpZero : exmax - 1022;     // max < 2^Ex
   if (i0 + i >= Iw) return;
   if (seg == 0) E[blockIdx.x * (int64_t)Rp + i0 + i] = Ex;
 #pragma unroll
@@ -187,23 +192,21 @@ oz_expo_kernel(const double *__restrict__ src, int64_t si, int64_t sk, int I, in
   const int64_t w = blockIdx.x;
   const int i = blockIdx.y * 256 + threadIdx.x;
   if (i >= Rp) return;
-  unsigned long long mx = 0;
+  // the largest exponent field is the largest high word (sign cleared), shifted: a
+  // 32-bit integer max (a 64-bit max of the bit patterns ran on the FP64 units)
+  uint32_t mx = 0;
   if (i < I) {
     const int64_t k0 = w * kWin;
     const int64_t kn = (K - k0) < kWin ? (K - k0) : kWin;
     const double *p = src + (int64_t)i * si + k0 * sk;
     if (kn == kWin) {
 #pragma unroll 16
-      for (int k = 0; k < kWin; ++k)
-        mx = max(mx, (unsigned long long)__double_as_longlong(__ldg(p + k * sk)) &
-                         0x7FFFFFFFFFFFFFFFull);
+      for (int k = 0; k < kWin; ++k) mx = max(mx, hi_abs(__ldg(p + k * sk)));
     } else {
-      for (int64_t k = 0; k < kn; ++k)
-        mx = max(mx, (unsigned long long)__double_as_longlong(__ldg(p + k * sk)) &
-                         0x7FFFFFFFFFFFFFFFull);
+      for (int64_t k = 0; k < kn; ++k) mx = max(mx, hi_abs(__ldg(p + k * sk)));
     }
   }
-  E[w * Rp + i] = mx == 0 ? kExpZero : (int)(mx >> 52) - 1022;
+  E[w * Rp + i] = (mx >> 20) == 0 ? kExpZero : (int)(mx >> 20) - 1022;
 }
 
 // ------------------------------------------------------------------------ products

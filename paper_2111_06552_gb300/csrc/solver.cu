@@ -488,10 +488,12 @@ class Engine {
     ProfScope ps(prof, GCGE_K_OTHER, 2.0 * n_ * k * sizeof(T), 0.0);
     return copy_cols<T, T>(n_, k, X, ldx, Y, ldy, nullptr, st_);
   }
-  int syev_small(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq) {
+  // fp32: a matrix of order <= 32 formed from FP32 blocks, diagonalised in FP32
+  int syev_small(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq,
+                 bool fp32 = false) {
     g_launches += 2;
     ProfScope ps(prof, GCGE_K_SYEV, 0.0, 0.0);
-    return syev(d, A, lda, w, Q, ldq, sw_, nullptr, st_);
+    return syev(d, A, lda, w, Q, ldq, sw_, nullptr, st_, fp32);
   }
   int borth(T *W, int m, const QPart *parts, int nparts, int *m_out);
   int normalize_drop(T *W, T *BW, int64_t ld, int m, double thr, int *m_out);
@@ -669,7 +671,9 @@ int Engine<T>::leaf(T *W, T *BW, int64_t ld, int len, int *out) {
     GCGE_CHECK(gramT(len, len, 1.0, W, ld, BW, ld, 0.0, Ms_, kLeaf));
     symmetrize_kernel<<<1, 256, 0, st_>>>(len, 0, Ms_, kLeaf);
     GCGE_LAUNCH_CHECK();
-    GCGE_CHECK(syev_small(len, Ms_, kLeaf, Ml_, Mq_, kLeaf));
+    // the FP32 engine's leaf Gram comes from FP32 blocks and its drop and repeat tests
+    // are at FP32 level: FP32 rotations suffice
+    GCGE_CHECK(syev_small(len, Ms_, kLeaf, Ml_, Mq_, kLeaf, sizeof(T) == 4));
     leaf_coeffs_kernel<<<1, 256, 0, st_>>>(len, Ml_, Mq_, kLeaf, th_.leaf_drop, th_.leaf_rel, Mc_,
                                            kLeaf, d_cnt_, d_crit_);
     GCGE_LAUNCH_CHECK();

@@ -184,21 +184,27 @@ jacobi_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restr
 }
 
 // Small matrices (d <= kSmallD): the whole Jacobi in one CTA with A and V in shared
-// memory and __syncthreads() between the two phases of a round.
+// memory and __syncthreads() between the two phases of a round.  R is the arithmetic:
+// FP64, or FP32 for matrices formed from FP32 data (the Algorithm 3 leaves of the FP32
+// phase, whose drop and repeat tests are at FP32 level): on GB300 a round of FP64
+// rotations waits on the FP64 units of one SM (two lanes per clock).
 constexpr int kSmallD = 32;
 
+template <typename R>
 __global__ void __launch_bounds__(256)
 jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *__restrict__ Vout,
                     int64_t ldv, int *__restrict__ flags, int max_sweeps) {
-  __shared__ double sA[kSmallD][kSmallD + 1];
-  __shared__ double sV[kSmallD][kSmallD + 1];
-  __shared__ double rot[kSmallD / 2][3];
+  constexpr R kRel = sizeof(R) == 8 ? R(1e-15) : R(1e-6);     // rotation threshold
+  constexpr R kTiny = sizeof(R) == 8 ? R(1e-300) : R(1e-30);
+  __shared__ R sA[kSmallD][kSmallD + 1];
+  __shared__ R sV[kSmallD][kSmallD + 1];
+  __shared__ R rot[kSmallD / 2][3];
   __shared__ int cnt;
   const int P = D / 2;
   for (int u = threadIdx.x; u < d * d; u += blockDim.x) {
     const int i = u % d, j = u / d;
-    sA[i][j] = A[i + (int64_t)j * lda];
-    sV[i][j] = (i == j) ? 1.0 : 0.0;
+    sA[i][j] = (R)A[i + (int64_t)j * lda];
+    sV[i][j] = (i == j) ? R(1) : R(0);
   }
   __syncthreads();
   int sweep = 0;
@@ -209,15 +215,15 @@ jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *_
       for (int k = threadIdx.x; k < P; k += blockDim.x) {
         int p, q;
         round_pair(D, r, k, p, q);
-        double c = 1.0, s = 0.0, t = 0.0;
+        R c = R(1), s = R(0), t = R(0);
         if (q < d) {
-          const double app = sA[p][p], aqq = sA[q][q], apq = sA[p][q];
+          const R app = sA[p][p], aqq = sA[q][q], apq = sA[p][q];
           if (apq != apq || app != app || aqq != aqq) flags[1] = 1;
-          const double thr = 1e-15 * sqrt(fabs(app) * fabs(aqq));
-          if (fabs(apq) > thr && fabs(apq) > 1e-300) {
-            const double th = (aqq - app) / (2.0 * apq);
-            t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
-            c = 1.0 / sqrt(1.0 + t * t);
+          const R thr = kRel * sqrt(fabs(app) * fabs(aqq));
+          if (fabs(apq) > thr && fabs(apq) > kTiny) {
+            const R th = (aqq - app) / (R(2) * apq);
+            t = (th >= R(0) ? R(1) : R(-1)) / (fabs(th) + sqrt(R(1) + th * th));
+            c = R(1) / sqrt(R(1) + t * t);
             s = t * c;
             atomicAdd(&cnt, 1);
           }
@@ -231,28 +237,28 @@ jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *_
       for (int u = threadIdx.x; u < nblk + d * P; u += blockDim.x) {
         if (u < nblk) {
           const int kr = u % P, kc = u / P;
-          const double s1 = rot[kr][1], s2 = rot[kc][1];
-          if (s1 == 0.0 && s2 == 0.0) continue;
+          const R s1 = rot[kr][1], s2 = rot[kc][1];
+          if (s1 == R(0) && s2 == R(0)) continue;
           int pr, qr, pc, qc;
           round_pair(D, r, kr, pr, qr);
           round_pair(D, r, kc, pc, qc);
           if (kr == kc) {
-            const double t = rot[kr][2];
-            const double apq = sA[pr][qr];
+            const R t = rot[kr][2];
+            const R apq = sA[pr][qr];
             sA[pr][pr] -= t * apq;
             sA[qr][qr] += t * apq;
-            sA[pr][qr] = 0.0;
-            sA[qr][pr] = 0.0;
+            sA[pr][qr] = R(0);
+            sA[qr][pr] = R(0);
             continue;
           }
-          const double c1 = rot[kr][0], c2 = rot[kc][0];
+          const R c1 = rot[kr][0], c2 = rot[kc][0];
           const bool vqr = qr < d, vqc = qc < d;
-          const double a = sA[pr][pc];
-          const double b = vqc ? sA[pr][qc] : 0.0;
-          const double e = vqr ? sA[qr][pc] : 0.0;
-          const double f = (vqr && vqc) ? sA[qr][qc] : 0.0;
-          const double a1 = c1 * a - s1 * e, b1 = c1 * b - s1 * f;
-          const double e1 = s1 * a + c1 * e, f1 = s1 * b + c1 * f;
+          const R a = sA[pr][pc];
+          const R b = vqc ? sA[pr][qc] : R(0);
+          const R e = vqr ? sA[qr][pc] : R(0);
+          const R f = (vqr && vqc) ? sA[qr][qc] : R(0);
+          const R a1 = c1 * a - s1 * e, b1 = c1 * b - s1 * f;
+          const R e1 = s1 * a + c1 * e, f1 = s1 * b + c1 * f;
           sA[pr][pc] = c2 * a1 - s2 * b1;
           if (vqc) sA[pr][qc] = s2 * a1 + c2 * b1;
           if (vqr) sA[qr][pc] = c2 * e1 - s2 * f1;
@@ -260,12 +266,12 @@ jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *_
         } else {
           const int v = u - nblk;
           const int k = v % P, i = v / P;
-          const double s = rot[k][1];
-          if (s == 0.0) continue;
-          const double c = rot[k][0];
+          const R s = rot[k][1];
+          if (s == R(0)) continue;
+          const R c = rot[k][0];
           int p, q;
           round_pair(D, r, k, p, q);
-          const double x = sV[i][p], y = sV[i][q];
+          const R x = sV[i][p], y = sV[i][q];
           sV[i][p] = c * x - s * y;
           sV[i][q] = s * x + c * y;
         }
@@ -280,8 +286,8 @@ jacobi_small_kernel(int d, int D, double *__restrict__ A, int64_t lda, double *_
   }
   for (int u = threadIdx.x; u < d * d; u += blockDim.x) {
     const int i = u % d, j = u / d;
-    A[i + (int64_t)j * lda] = sA[i][j];
-    Vout[i + (int64_t)j * ldv] = sV[i][j];
+    A[i + (int64_t)j * lda] = (double)sA[i][j];
+    Vout[i + (int64_t)j * ldv] = (double)sV[i][j];
   }
   if (threadIdx.x == 0) flags[2] = sweep;
 }
@@ -335,7 +341,7 @@ void SyevWork::free_all() {
 }
 
 int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevWork &work,
-         int *sweeps, cudaStream_t st) {
+         int *sweeps, cudaStream_t st, bool fp32_small) {
   if (d <= 0) return GCGE_OK;
   GCGE_CHECK(work.alloc(d));
   const int D = d + (d & 1);
@@ -362,7 +368,10 @@ int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevW
   double *Vw = work.V;
   int64_t ldv = d;
   if (d <= kSmallD) {
-    jacobi_small_kernel<<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);
+    if (fp32_small)
+      jacobi_small_kernel<float><<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);
+    else
+      jacobi_small_kernel<double><<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);
     GCGE_LAUNCH_CHECK();
   } else {
     void *args[] = {&d, (void *)&D, &A, &lda, &Vw, &ldv, &work.rot, &work.sync, &work.flags,

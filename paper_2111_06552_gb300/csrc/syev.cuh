@@ -39,7 +39,9 @@ int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_
 
 // A (d x d col-major, lda) is destroyed; w[d] ascending; Q (ldq) eigenvectors.
 // Synchronises the stream.  Returns GCGE_OK / GCGE_ETIMEOUT / GCGE_ENAN / GCGE_ECUDA.
+// fp32_small: matrices of order <= 32 are diagonalised in FP32 arithmetic (for
+// matrices formed from FP32 data); results are returned in FP64 either way.
 int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevWork &work,
-         int *sweeps, cudaStream_t st);
+         int *sweeps, cudaStream_t st, bool fp32_small = false);
 
 }  // namespace gcge
