@@ -414,15 +414,6 @@ __global__ void col_dots_kernel(int64_t n, int k, const T *__restrict__ X, int64
   }
 }
 
-__global__ void sum_parts_kernel(int k, int parts, const double *__restrict__ part,
-                                 double *__restrict__ out) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < parts; ++p) s += part[(int64_t)p * k + j];
-    out[j] = s;
-  }
-}
-
 template <typename T>
 __global__ void residual_kernel(int64_t n, int m, const T *__restrict__ X, int64_t ldx,
                                 const T *__restrict__ AX, int64_t lda, const T *__restrict__ BX,
@@ -706,7 +697,8 @@ int col_dots(int64_t n, int k, const T *X, int64_t ldx, const T *Y, int64_t ldy,
   col_dots_kernel<T><<<g, kRedThreads, kRedThreads * sizeof(double), st>>>(n, k, X, ldx, Y, ldy,
                                                                            part);
   GCGE_LAUNCH_CHECK();
-  sum_parts_kernel<<<ceil_div(k, 256), 256, 0, st>>>(k, g, part, out);
+  // out[j] = sum over the g partial rows (the split-K reduction of the Gram products)
+  gram_reduce_kernel<<<red_blocks(k), 32 * kRedGroups, 0, st>>>(k, 1, g, part, 1.0, 0.0, out, k);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
@@ -722,7 +714,8 @@ int residual_parts(int64_t n, int m, const T *X, int64_t ldx, const T *AX, int64
   residual_kernel<T><<<g, kRedThreads, 2 * kRedThreads * sizeof(double), st>>>(
       n, m, X, ldx, AX, lda, BX, ldb, lam, part);
   GCGE_LAUNCH_CHECK();
-  sum_parts_kernel<<<ceil_div(2 * m, 256), 256, 0, st>>>(2 * m, g, part, out);
+  gram_reduce_kernel<<<red_blocks(2 * m), 32 * kRedGroups, 0, st>>>(2 * m, 1, g, part, 1.0, 0.0,
+                                                                     out, 2 * m);
   GCGE_LAUNCH_CHECK();
   return GCGE_OK;
 }
