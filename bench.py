@@ -210,10 +210,12 @@ FP64_PEAK_TFLOPS = 1.25
 OZ_PAIRS = 28
 
 # DRAM traffic (read + write) over algorithmic bytes per kernel class, measured by ncu
-# on each class's kernel at the headline workload's shapes (summaries in profiles/);
-# None where the kernel changed after its counters were taken.
-TRAFFIC_RATIO = {"q1_64": {"spmm": None, "gram": 1.05, "vc": 0.88, "spmm64": None,
-                           "gram64": 1.01, "vc64": 3.30, "gram64tc": None, "vc64tc": None}}
+# on each class's kernel at the headline workload's shapes (k = 20 for the SpMM: the CG
+# variant with the fused dot 0.83, the plain one 0.84; FP64 SpMM 0.87); None where the
+# kernel changed after its counters were taken or the class mixes shapes whose traffic
+# differs (the emulated FP64 products).
+TRAFFIC_RATIO = {"q1_64": {"spmm": 0.83, "gram": 1.05, "vc": 0.88, "spmm64": 0.87,
+                           "gram64": None, "vc64": None, "gram64tc": None, "vc64tc": None}}
 
 
 def traffic_per_launch(config, cls, prof):

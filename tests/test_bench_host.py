@@ -83,12 +83,13 @@ def test_spmm64_reported_against_hbm_when_that_fraction_is_larger():
 
 def test_traffic_per_launch_scales_algorithmic_bytes():
     prof = _prof(1.0, 4, 4e8, 0.0)
-    r = bench.TRAFFIC_RATIO["q1_64"]["vc64"]
-    assert bench.traffic_per_launch("q1_64", "vc64", prof) == round(r * 1e8)
+    r = bench.TRAFFIC_RATIO["q1_64"]["spmm"]
+    assert bench.traffic_per_launch("q1_64", "spmm", prof) == round(r * 1e8)
     assert bench.traffic_per_launch("q1_64", "syev", prof) is None
     assert bench.traffic_per_launch("q1_64", "gram64tc", prof) is None   # not measured
-    assert bench.traffic_per_launch("other_workload", "vc64", prof) is None
-    assert bench.traffic_per_launch("q1_64", "vc64", _prof(1.0, 0, 0.0, 0.0)) is None
+    assert bench.traffic_per_launch("q1_64", "vc64", prof) is None       # kernel changed
+    assert bench.traffic_per_launch("other_workload", "spmm", prof) is None
+    assert bench.traffic_per_launch("q1_64", "spmm", _prof(1.0, 0, 0.0, 0.0)) is None
 
 
 def test_measured_peaks_file_and_fallback(tmp_path, monkeypatch):
