@@ -181,6 +181,46 @@ def test_syev_matches_oracle(g, d):
     assert sweeps < 30
 
 
+def _structured_abar(rng, nx, npp, nw, scale):
+    """A Rayleigh-Ritz matrix with the structure of Eq. (struct_bar_A_new): diagonal Ritz
+    values on the X block, zero X-P coupling, a dense P block and W coupled to both."""
+    lam = np.sort(3 * np.pi ** 2 * (1 + 30 * rng.random(nx)))
+    d = nx + npp + nw
+    A = np.zeros((d, d))
+    A[:nx, :nx] = np.diag(lam)
+    M = rng.standard_normal((npp, npp))
+    A[nx:nx + npp, nx:nx + npp] = lam[-1] * (M @ M.T / npp + np.eye(npp))
+    Bx = scale * lam[:, None] * rng.standard_normal((nx, nw))
+    A[:nx, nx + npp:] = Bx
+    A[nx + npp:, :nx] = Bx.T
+    Bp = scale * lam[-1] * rng.standard_normal((npp, nw))
+    A[nx:nx + npp, nx + npp:] = Bp
+    A[nx + npp:, nx:nx + npp] = Bp.T
+    G = rng.standard_normal((nw, nw))
+    A[nx + npp:, nx + npp:] = 2 * lam[-1] * (G @ G.T / nw + np.eye(nw))
+    return A
+
+
+@pytest.mark.parametrize("scale", [1e-1, 1e-4])
+def test_syev_structured_rr_matrix_d500(g, scale):
+    """The order of the first Rayleigh-Ritz matrix of the 160^3 workload (sizeX 300 +
+    P 100 + W 100), with strong and weak coupling, against LAPACK."""
+    import torch
+    rng = np.random.default_rng(int(-np.log10(scale)))
+    M = _structured_abar(rng, 300, 100, 100, scale)
+    d = M.shape[0]
+    w_ref, _ = L.sym_eig(M)
+    wd = torch.zeros(d, dtype=torch.float64, device="cuda")
+    Qd = torch.zeros((d, d), dtype=torch.float64, device="cuda")
+    g.gcge_syev(d, dev(M.T.copy()), d, wd, Qd, d)
+    w = host(wd)
+    Qh = host(Qd).T
+    nrm = np.abs(w_ref).max()
+    assert np.abs(w - w_ref).max() <= 1e-13 * nrm * max(1.0, np.sqrt(d) / 4)
+    assert np.abs(Qh.T @ Qh - np.eye(d)).max() <= 1e-13 * d
+    assert np.abs(M @ Qh - Qh * w).max() <= 1e-12 * nrm
+
+
 def test_syev_degenerate_and_diagonal(g):
     import torch
     for M in (np.eye(8), np.diag(np.arange(10.0)[::-1]), np.zeros((5, 5))):
