@@ -20,9 +20,10 @@
 //    scale 2^-7(i+j); the pairs of one scale accumulate in their own tensor-memory
 //    accumulator (seven of them), where every partial sum is an integer below 2^24 in
 //    magnitude (128 rows x at most 7 pairs x 127^2), so all seven sums are exact.
-//    The dropped pairs (i + j >= 9) and the digit truncation bound the error: about
-//    2^-47 max|x| max|y| per term (window maxima), against about 2^-53 sqrt(n)
-//    Sum|x||y| for an FP64 dot product of n terms.
+//    The digit rounding of both operands and the dropped pairs (i + j >= 9) bound the
+//    error by 2^(E_x + E_y - 46) per term (at most 2^-44 max|x| max|y|, window maxima;
+//    about 2^-47 on random data), against about 2^-53 sqrt(n) Sum|x||y| for an FP64
+//    dot product of n terms.
 //  * Drain.  After each window the seven accumulators are read (tcgen05.ld),
 //    turned into integers and combined exactly in int64, converted once, scaled by
 //    the window's 2^(E_x + E_y) and added to FP64 registers.
