@@ -491,6 +491,7 @@ class Engine {
   // fp32: a matrix of order <= 32 formed from FP32 blocks, diagonalised in FP32
   int syev_small(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq,
                  bool fp32 = false) {
+    // (the Algorithm 3 leaves are of order <= 16: fp32 selects FP32 rotations)
     g_launches += 2;
     ProfScope ps(prof, GCGE_K_SYEV, 0.0, 0.0);
     return syev(d, A, lda, w, Q, ldq, sw_, nullptr, st_, fp32);
@@ -950,7 +951,9 @@ int Engine<T>::rayleigh_ritz(bool first, int d) {
   int s;
   {
     ProfScope ps(prof, GCGE_K_SYEV, 0.0, 0.0);
-    s = syev(d, Abar_, lda, theta_, Qe_, lda, sw_, nullptr, st_);
+    // the FP32 engine's Abar comes from FP32 products: refining its eigenvectors beyond
+    // 1e-10 buys nothing
+    s = syev(d, Abar_, lda, theta_, Qe_, lda, sw_, nullptr, st_, sizeof(T) == 4);
   }
   ms_syev += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return s;

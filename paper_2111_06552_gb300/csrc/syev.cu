@@ -341,7 +341,7 @@ void SyevWork::free_all() {
 }
 
 int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevWork &work,
-         int *sweeps, cudaStream_t st, bool fp32_small) {
+         int *sweeps, cudaStream_t st, bool fp32_data) {
   if (d <= 0) return GCGE_OK;
   GCGE_CHECK(work.alloc(d));
   const int D = d + (d & 1);
@@ -356,7 +356,8 @@ int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevW
   GCGE_CUDA(cudaMemsetAsync(work.sync, 0, sizeof(unsigned) * 8, st));
   GCGE_CUDA(cudaMemsetAsync(work.flags, 0, sizeof(int) * 4, st));
   if (work.mixed && d > kSmallD) {
-    const int s = syev_mixed(d, A, lda, w, Q, ldq, work.mp, work.flags, sweeps, st);
+    const int s = syev_mixed(d, A, lda, w, Q, ldq, work.mp, work.flags, sweeps, st,
+                             fp32_data ? 1e-10 : 1e-13);
     if (s == GCGE_OK) {
       GCGE_CUDA(cudaStreamSynchronize(st));
       return GCGE_OK;
@@ -368,7 +369,7 @@ int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevW
   double *Vw = work.V;
   int64_t ldv = d;
   if (d <= kSmallD) {
-    if (fp32_small)
+    if (fp32_data)
       jacobi_small_kernel<float><<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);
     else
       jacobi_small_kernel<double><<<1, 256, 0, st>>>(d, D, A, lda, Vw, ldv, work.flags, max_sweeps);

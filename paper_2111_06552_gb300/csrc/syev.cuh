@@ -34,14 +34,18 @@ struct SyevWork {
 // Mixed-precision eigensolve of the symmetric A (not modified); GCGE_EINVAL when it
 // does not apply (size, a cluster of near-equal eigenvalues wider than 32, or no
 // convergence), in which case the caller uses the FP64 Jacobi.
+// off_tol: the refinement stops once the largest off-diagonal of V^T A V is below
+// off_tol of its largest diagonal entry (1e-13: FP64 eigenvectors).
 int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_t ldq,
-               MpWork &mw, int *flags_dev, int *sweeps, cudaStream_t st);
+               MpWork &mw, int *flags_dev, int *sweeps, cudaStream_t st,
+               double off_tol = 1e-13);
 
 // A (d x d col-major, lda) is destroyed; w[d] ascending; Q (ldq) eigenvectors.
 // Synchronises the stream.  Returns GCGE_OK / GCGE_ETIMEOUT / GCGE_ENAN / GCGE_ECUDA.
-// fp32_small: matrices of order <= 32 are diagonalised in FP32 arithmetic (for
-// matrices formed from FP32 data); results are returned in FP64 either way.
+// fp32_data: A was formed from FP32 blocks (entries accurate to about 1e-7): matrices
+// of order <= 32 are diagonalised in FP32 arithmetic and larger ones refined to 1e-10
+// instead of 1e-13; results are returned in FP64 either way.
 int syev(int d, double *A, int64_t lda, double *w, double *Q, int64_t ldq, SyevWork &work,
-         int *sweeps, cudaStream_t st, bool fp32_small = false);
+         int *sweeps, cudaStream_t st, bool fp32_data = false);
 
 }  // namespace gcge

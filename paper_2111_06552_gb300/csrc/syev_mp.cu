@@ -582,7 +582,7 @@ void MpWork::free_all() {
 // Returns GCGE_OK, or GCGE_EINVAL when this method does not apply (then the caller
 // falls back to the FP64 Jacobi); A is not modified.
 int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_t ldq,
-               MpWork &mw, int *flags_dev, int *sweeps, cudaStream_t st) {
+               MpWork &mw, int *flags_dev, int *sweeps, cudaStream_t st, double off_tol) {
   OjPlan pl;
   if (d < 2 || !oj_plan(d, pl)) return GCGE_EINVAL;
   GCGE_CHECK(mw.alloc(d));
@@ -651,7 +651,7 @@ int syev_mixed(int d, const double *A, int64_t lda, double *w, double *Q, int64_
     const double off = mw.h[0], nrm = mw.h[1];
     // done at 1e-13 of the norm, or once the off-diagonal stops shrinking near the
     // rounding level of the FP64 products (about d eps of the norm)
-    if (off <= 1e-13 * nrm || (off <= 1e-11 * nrm && off > 0.25 * prev_off)) {
+    if (off <= off_tol * nrm || (off <= 1e-11 * nrm && off > 0.25 * prev_off)) {
       converged = true;
       break;
     }
