@@ -687,6 +687,8 @@ int oz_vc(int64_t n, int d, int q, double alpha, const double *V, int64_t ldv, c
   // the rows of V are taken in chunks only to bound the exponent table (one int per row
   // and window); V's digits are cut inside the product
   int64_t rchunk = (int64_t)std::max<size_t>(128, kPlaneBudget / ((size_t)nwin * 4));
+  // a chunk's 128-row tiles are the product's grid.y (at most 65535)
+  rchunk = std::min<int64_t>(rchunk, (int64_t)65535 * 128);
   rchunk = std::min<int64_t>(round_up(n, 128), (rchunk / 128) * 128);
   const int RpA = (int)rchunk;
   const size_t bytes = (size_t)kDigits * RpB * Kp * 2 + (size_t)nwin * RpB * 4 +
