@@ -119,3 +119,9 @@ def test_reference_arm_reports_its_own_step_time(monkeypatch):
     assert line["cpu_baseline"]["sparse_threads"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
     assert bench.run_reference(A(), 1, 2) is None        # only rank 0 prints
+
+
+def test_table_workload_filter_rejects_unknown_names(monkeypatch):
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--table", "--workloads", "q1_64,nope"])
+    with pytest.raises(SystemExit, match="unknown workload 'nope'"):
+        bench.main()
